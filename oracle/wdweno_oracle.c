@@ -1,0 +1,330 @@
+/*
+ * FP64 CPU oracle for the Weighted-Direction (WD) WENO 2x zoom.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is compiled into liboracle.so and is
+ * loaded by the test-suite, by the smoke check and by the CPU-baseline leg of
+ * the benchmark.  The CUDA library never links, includes or calls it, and it
+ * never includes anything from the CUDA library.
+ *
+ * Source: B. Crnkovic, J. Skific, T. Bosner, "WENO based adaptive image zooming
+ * algorithm" (arXiv 2312.00229).
+ *   Sec. 2, Eq. (IzrazOmega) ............. alpha = C / (eps_h + SI)^beta,
+ *                                           eps_h = K_eps h^2
+ *   Sec. 3, Fig. inputdata ................ fine grid: even-even points are the
+ *                                           input samples, odd-odd points are
+ *                                           "x" points, mixed points are "+".
+ *   Sec. 3.1, Eqs. (Vektor), (p) .......... stencil {c-d, c+d, c+3d}; p is the
+ *                                           quadratic through it, taken at c.
+ *   Sec. 3.1, Eq. (2Dsmoothness) .......... directional smoothness indicator.
+ *   Sec. 3.1, Eq. (2DsmoothnessFinal) ..... D = SI + h^2/4 * (4 axis neighbours
+ *                                           at fine offset 2, same direction).
+ *   Sec. 3.1, Eqs. (alpha), (IzrazOmega2d), (2dKombinacija); Algorithm 1.
+ *   Sec. 3.2, Eq. (tezine) ................ D for "+" points uses the four
+ *                                           diagonal neighbours at fine offset 1.
+ *   Sec. 3.2, Eqs. (IzrazOmega2dRavno), (2dKombinacijaRavno); Algorithm 2.
+ *
+ * Readings of passages that the paper leaves open (each is a parameter or a
+ * fixed choice here, listed in the design notes):
+ *   - boundary: the paper gives none.  The method is evaluated on the
+ *     infinite extension of the coarse image given by `boundary` (clamp to
+ *     edge by default) and then cropped.
+ *   - d^gamma (Eq. Vektor, garbled): one fine-grid step along gamma.
+ *   - SI scale (Eq. 2Dsmoothness): "normalized" uses the stencil's own node
+ *     spacing 2|d| as the length scale in both phases; "literal" uses sqrt(2)h
+ *     in both phases, as printed.
+ *   - neighbour weight h^2/4 (the definitions, not the h^2/8 of the proof).
+ *   - all four directions k = 0..3 (the sums in Eqs. IzrazOmega2d and
+ *     2dKombinacija run over four; the loop bound printed in the algorithms
+ *     visits three).
+ *
+ * Everything is computed in double precision with plain loops over a
+ * fine-grid array; every computed point records that it was computed, and the
+ * crop step checks that each output point was.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "wdweno_oracle.h"
+
+/* Coarse ghost cells added on each side before the method runs.  The output
+ * footprint of one coarse cell is 4 cells before and 5 after it, so 6 is
+ * enough; the test-suite checks that a larger ghost width gives the same
+ * result. */
+#ifndef ORACLE_GHOST
+#define ORACLE_GHOST 6
+#endif
+
+oracle_params oracle_params_default(void) {
+  oracle_params p;
+  p.beta = 2.0;   /* Sec. 4: beta = 2 unless stated otherwise */
+  p.k_eps = 1e-8; /* Sec. 2: K_eps = 1e-8 */
+  p.h = 1.0;      /* pixel units */
+  p.si_scale = ORACLE_SI_NORMALIZED;
+  p.out_mode = ORACLE_OUT_2N;
+  p.boundary = ORACLE_BC_CLAMP;
+  p.ghost = ORACLE_GHOST;
+  return p;
+}
+
+/* Maps an integer coarse index onto [0, n) under the boundary rule, or
+ * returns -1 when the rule supplies the value 0 there. */
+static int64_t extend_index(int64_t i, int64_t n, int rule) {
+  if (i >= 0 && i < n) return i;
+  switch (rule) {
+    case ORACLE_BC_CLAMP:
+      return i < 0 ? 0 : n - 1;
+    case ORACLE_BC_ZERO:
+      return -1;
+    case ORACLE_BC_REFLECT101: { /* ... 2 1 | 0 1 2 ... n-1 | n-2 ... */
+      if (n == 1) return 0;
+      int64_t period = 2 * (n - 1);
+      int64_t r = i % period;
+      if (r < 0) r += period;
+      return r < n ? r : period - r;
+    }
+    case ORACLE_BC_SYMMETRIC: { /* ... 1 0 | 0 1 ... n-1 | n-1 n-2 ... */
+      int64_t period = 2 * n;
+      int64_t r = i % period;
+      if (r < 0) r += period;
+      return r < n ? r : period - 1 - r;
+    }
+    default:
+      return i < 0 ? 0 : n - 1;
+  }
+}
+
+/* The quadratic p through the three stencil nodes of Eq. (p).  In the local
+ * coordinate t along the direction, measured in units of |d|, the nodes are
+ * at t = -1 (c - d), t = 1 (c + d) and t = 3 (c + 3d).  Newton form:
+ *   p(t) = N0 + f01 (t + 1) + f012 (t + 1)(t - 1)
+ * with divided differences f01 = [N0,N1], f012 = [N0,N1,N2]. */
+typedef struct {
+  double value_at_centre; /* p(0) */
+  double d1_const;        /* p'(t)  = d1_const + d1_slope * t */
+  double d1_slope;
+  double d2;              /* p''(t) = d2 */
+} quad_t;
+
+static quad_t quadratic_through(double n0, double n1, double n2) {
+  const double t0 = -1.0, t1 = 1.0, t2 = 3.0;
+  double f01 = (n1 - n0) / (t1 - t0);
+  double f12 = (n2 - n1) / (t2 - t1);
+  double f012 = (f12 - f01) / (t2 - t0);
+  quad_t q;
+  /* p(0) = N0 + f01 (0 - t0) + f012 (0 - t0)(0 - t1) */
+  q.value_at_centre = n0 + f01 * (0.0 - t0) + f012 * (0.0 - t0) * (0.0 - t1);
+  /* p'(t) = f01 + f012 ((t - t0) + (t - t1)) = f01 - f012 (t0 + t1) + 2 f012 t */
+  q.d1_const = f01 - f012 * (t0 + t1);
+  q.d1_slope = 2.0 * f012;
+  q.d2 = 2.0 * f012;
+  return q;
+}
+
+/* Exact integral over t in [-1, 1] of (a + b t)^2. */
+static double int_sq_linear(double a, double b) {
+  return 2.0 * a * a + (2.0 / 3.0) * b * b;
+}
+
+/* Eq. (2Dsmoothness): SI = sum_{l=1,2} int_{c-d}^{c+d} L^{2l-1} (d^l p/dx^l)^2 dx,
+ * where x is arc length along the direction and L is the length scale.
+ * With x = |d| t:  d^l p/dx^l = |d|^{-l} d^l p/dt^l and dx = |d| dt, so the
+ * l-th term is (L/|d|)^{2l-1} * int_{-1}^{1} (d^l p/dt^l)^2 dt. */
+static double smoothness_indicator(const quad_t* q, double scale_over_step) {
+  double r1 = scale_over_step;                /* (L/|d|)^1 */
+  double r3 = scale_over_step * scale_over_step * scale_over_step; /* ^3 */
+  double i1 = int_sq_linear(q->d1_const, q->d1_slope);
+  double i2 = int_sq_linear(q->d2, 0.0);
+  return r1 * i1 + r3 * i2;
+}
+
+/* One phase of Algorithms 1/2 on the fine grid.
+ *   F, have  : fine-grid values and "computed" flags (FR x FC, row-major)
+ *   dirs     : the four direction steps (dP, dQ) in fine-index units
+ *   nbr      : the four neighbour offsets used by D (Eq. 2DsmoothnessFinal
+ *              for phase 1, Eq. tezine for phase 2)
+ *   is_target: which fine points this phase computes
+ *   scale_over_step: L/|d| for the smoothness indicator
+ */
+typedef int (*target_fn)(int64_t P, int64_t Q);
+
+static int is_cross_point(int64_t P, int64_t Q) { return (P & 1) && (Q & 1); }
+static int is_plus_point(int64_t P, int64_t Q) { return ((P + Q) & 1) != 0; }
+
+static int run_phase(double* F, unsigned char* have, int64_t FR, int64_t FC,
+                     const int dirs[4][2], const int nbr[4][2], target_fn is_target,
+                     double scale_over_step, const oracle_params* prm) {
+  const int64_t N = FR * FC;
+  double* p = (double*)malloc(sizeof(double) * N);
+  double* si = (double*)malloc(sizeof(double) * N);
+  unsigned char* have_si = (unsigned char*)malloc(N);
+  double* usum = (double*)calloc(N, sizeof(double));
+  double* asum = (double*)calloc(N, sizeof(double));
+  unsigned char* nterms = (unsigned char*)calloc(N, 1);
+  if (!p || !si || !have_si || !usum || !asum || !nterms) {
+    free(p); free(si); free(have_si); free(usum); free(asum); free(nterms);
+    return ORACLE_ENOMEM;
+  }
+  const double eps_h = prm->k_eps * prm->h * prm->h; /* Sec. 2 */
+  const double nbr_w = prm->h * prm->h / 4.0;        /* Eqs. 2DsmoothnessFinal, tezine */
+
+  for (int k = 0; k < 4; ++k) {
+    const int dP = dirs[k][0], dQ = dirs[k][1];
+    memset(have_si, 0, N);
+    /* First sweep: p and SI at every target point whose stencil is known. */
+    for (int64_t P = 0; P < FR; ++P) {
+      for (int64_t Q = 0; Q < FC; ++Q) {
+        if (!is_target(P, Q)) continue;
+        int64_t P0 = P - dP, Q0 = Q - dQ;         /* c - d  */
+        int64_t P1 = P + dP, Q1 = Q + dQ;         /* c + d  */
+        int64_t P2 = P + 3 * dP, Q2 = Q + 3 * dQ; /* c + 3d */
+        if (P0 < 0 || P0 >= FR || P2 < 0 || P2 >= FR) continue;
+        if (Q0 < 0 || Q0 >= FC || Q2 < 0 || Q2 >= FC) continue;
+        if (!have[P0 * FC + Q0] || !have[P1 * FC + Q1] || !have[P2 * FC + Q2]) continue;
+        quad_t q = quadratic_through(F[P0 * FC + Q0], F[P1 * FC + Q1], F[P2 * FC + Q2]);
+        p[P * FC + Q] = q.value_at_centre;
+        si[P * FC + Q] = smoothness_indicator(&q, scale_over_step);
+        have_si[P * FC + Q] = 1;
+      }
+    }
+    /* Second sweep: D, alpha, and the running sums of alpha*p and alpha. */
+    for (int64_t P = 0; P < FR; ++P) {
+      for (int64_t Q = 0; Q < FC; ++Q) {
+        if (!is_target(P, Q) || !have_si[P * FC + Q]) continue;
+        double nsum = 0.0;
+        int ok = 1;
+        for (int t = 0; t < 4 && ok; ++t) {
+          int64_t Pn = P + nbr[t][0], Qn = Q + nbr[t][1];
+          if (Pn < 0 || Pn >= FR || Qn < 0 || Qn >= FC || !have_si[Pn * FC + Qn]) {
+            ok = 0;
+          } else {
+            nsum += si[Pn * FC + Qn];
+          }
+        }
+        if (!ok) continue;
+        double D = si[P * FC + Q] + nbr_w * nsum;
+        double alpha = 0.5 / pow(eps_h + D, prm->beta); /* Eq. (alpha) */
+        usum[P * FC + Q] += alpha * p[P * FC + Q];
+        asum[P * FC + Q] += alpha;
+        nterms[P * FC + Q] += 1;
+      }
+    }
+  }
+  /* Normalisation (Eqs. IzrazOmega2d / IzrazOmega2dRavno). */
+  for (int64_t P = 0; P < FR; ++P) {
+    for (int64_t Q = 0; Q < FC; ++Q) {
+      if (!is_target(P, Q) || nterms[P * FC + Q] != 4) continue;
+      F[P * FC + Q] = usum[P * FC + Q] / asum[P * FC + Q];
+      have[P * FC + Q] = 1;
+    }
+  }
+  free(p); free(si); free(have_si); free(usum); free(asum); free(nterms);
+  return ORACLE_OK;
+}
+
+int oracle_zoom2x(const double* A, int64_t n, int64_t m, double* U,
+                  const oracle_params* prm) {
+  if (!A || !U || !prm || n < 1 || m < 1) return ORACLE_EINVAL;
+  if (prm->ghost < 5) return ORACLE_EINVAL;
+  const int64_t G = prm->ghost;
+  const int64_t ne = n + 2 * G, me = m + 2 * G; /* extended coarse grid */
+  const int64_t FR = 2 * ne - 1, FC = 2 * me - 1;
+  const int64_t N = FR * FC;
+  double* F = (double*)calloc(N, sizeof(double));
+  unsigned char* have = (unsigned char*)calloc(N, 1);
+  if (!F || !have) { free(F); free(have); return ORACLE_ENOMEM; }
+
+  /* Even-even fine points carry the (extended) input samples. */
+  for (int64_t I = 0; I < ne; ++I) {
+    int64_t i = extend_index(I - G, n, prm->boundary);
+    for (int64_t J = 0; J < me; ++J) {
+      int64_t j = extend_index(J - G, m, prm->boundary);
+      double v = (i < 0 || j < 0) ? 0.0 : A[i * m + j];
+      F[(2 * I) * FC + 2 * J] = v;
+      have[(2 * I) * FC + 2 * J] = 1;
+    }
+  }
+
+  /* Phase 1 (Sec. 3.1, Algorithm 1): gamma_k = pi/4 + k pi/2.  With the
+   * first fine index along x and the second along y, one fine step along
+   * gamma_k is (cos, sin) scaled to the grid: */
+  static const int diag_dirs[4][2] = {{1, 1}, {-1, 1}, {-1, -1}, {1, -1}};
+  /* Eq. (2DsmoothnessFinal): neighbours at (i, j+-2) and (i+-2, j). */
+  static const int diag_nbr[4][2] = {{0, 2}, {2, 0}, {0, -2}, {-2, 0}};
+  /* Phase 2 (Sec. 3.2, Algorithm 2): gamma_k = k pi/2. */
+  static const int axis_dirs[4][2] = {{1, 0}, {0, 1}, {-1, 0}, {0, -1}};
+  /* Eq. (tezine): neighbours at (i+-1, j+-1). */
+  static const int axis_nbr[4][2] = {{1, 1}, {-1, -1}, {-1, 1}, {1, -1}};
+
+  /* Length-scale ratio L/|d| of the smoothness indicator.  Normalized: L is
+   * the node spacing 2|d| in both phases.  Literal: L = sqrt(2) h with
+   * |d| = h/sqrt(2) on diagonals and h/2 on axes. */
+  double r1, r2;
+  if (prm->si_scale == ORACLE_SI_LITERAL) {
+    r1 = sqrt(2.0) / (1.0 / sqrt(2.0)); /* = 2 */
+    r2 = sqrt(2.0) / 0.5;               /* = 2 sqrt(2) */
+  } else {
+    r1 = 2.0;
+    r2 = 2.0;
+  }
+
+  int rc = run_phase(F, have, FR, FC, diag_dirs, diag_nbr, is_cross_point, r1, prm);
+  if (rc == ORACLE_OK)
+    rc = run_phase(F, have, FR, FC, axis_dirs, axis_nbr, is_plus_point, r2, prm);
+
+  if (rc == ORACLE_OK) {
+    const int64_t orows = prm->out_mode == ORACLE_OUT_2N_MINUS_1 ? 2 * n - 1 : 2 * n;
+    const int64_t ocols = prm->out_mode == ORACLE_OUT_2N_MINUS_1 ? 2 * m - 1 : 2 * m;
+    for (int64_t pr = 0; pr < orows && rc == ORACLE_OK; ++pr) {
+      for (int64_t qc = 0; qc < ocols; ++qc) {
+        int64_t P = pr + 2 * G, Q = qc + 2 * G;
+        if (!have[P * FC + Q]) { rc = ORACLE_EFOOTPRINT; break; }
+        U[pr * ocols + qc] = F[P * FC + Q];
+      }
+    }
+  }
+  free(F);
+  free(have);
+  return rc;
+}
+
+int oracle_zoom2x_planes(const double* A, int64_t planes, int64_t n, int64_t m,
+                         double* U, const oracle_params* prm) {
+  if (!prm) return ORACLE_EINVAL;
+  const int64_t orows = prm->out_mode == ORACLE_OUT_2N_MINUS_1 ? 2 * n - 1 : 2 * n;
+  const int64_t ocols = prm->out_mode == ORACLE_OUT_2N_MINUS_1 ? 2 * m - 1 : 2 * m;
+  int rc = ORACLE_OK;
+  /* Planes are independent (the method runs per channel). */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1) reduction(min : rc)
+#endif
+  for (int64_t c = 0; c < planes; ++c) {
+    int r = oracle_zoom2x(A + c * n * m, n, m, U + c * orows * ocols, prm);
+    if (r < rc) rc = r;
+  }
+  return rc;
+}
+
+/* uint8 encoding of an output value decoded to [0, 1]: saturate, scale by
+ * 255 and round half to even (the default rounding direction of nearbyint). */
+void oracle_encode_u8(const double* U, int64_t count, unsigned char* out) {
+  for (int64_t i = 0; i < count; ++i) {
+    double v = U[i];
+    if (!(v > 0.0)) v = 0.0; /* also maps NaN to 0 */
+    if (v > 1.0) v = 1.0;
+    out[i] = (unsigned char)nearbyint(v * 255.0);
+  }
+}
+
+int oracle_ghost_default(void) { return ORACLE_GHOST; }
+
+/* The two per-direction quantities of Eqs. (p) and (2Dsmoothness) for one
+ * stencil, exposed so that tests can check them against an independent
+ * quadrature. */
+void oracle_directional(double n0, double n1, double n2, double scale_over_step,
+                        double* p, double* si) {
+  quad_t q = quadratic_through(n0, n1, n2);
+  if (p) *p = q.value_at_centre;
+  if (si) *si = smoothness_indicator(&q, scale_over_step);
+}
