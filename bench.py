@@ -1,0 +1,505 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 WD WENO 2x zoom (arXiv 2312.00229, Sec. 3).
+
+Headline (one JSON line on rank 0): forward 2x zoom of a 1920x1080 RGB
+uint8 piecewise-smooth scene to 3840x2160, FP32 arithmetic, output Gpix/s
+(output pixels of all channels counted once per pixel), inputs resident in
+HBM.  One step = one launch of the fused forward kernel over the whole image.
+16 input/output buffer sets (~500 MB) rotate so that no step finds its data
+in the 129 MB L2; the launches are replayed from a CUDA graph.
+
+The same line carries the roofline of the forward kernel, the FP64 CPU
+oracle timed on the host cores (cpu_baseline), the end-to-end figure through
+the public API with host buffers (e2e), clocks sampled during the timed
+region, and the other parts of the metric: fwd+bwd Gpix/s (32x3x512x512 FP32,
+autograd step with an L2 loss), batched vs plain (256 uneven FP16 images in
+one persistent launch), the storage-format sweep on 3840x2160x3 and the 8x
+cascade of a 512x512 pixel-art image.
+
+``--impl reference`` times the FP64 oracle (the only other implementation
+of this method; the paper's own code is not published) on the host cores
+for the same metric.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "2x WENO zoom output Gpix/s & %HBM roofline; fwd+bwd Gpix/s; batched vs plain"
+WORKLOAD = "1920x1080x3 uint8 piecewise-smooth scene -> 3840x2160x3 uint8, FP32 arithmetic"
+H, W, C = 1080, 1920, 3
+OUT_PX = (2 * H) * (2 * W)  # output pixels per step (all channels per pixel)
+# Algorithmic FP32 operations per input pixel-channel (FMA counted once) of
+# the fused forward pass, beta = 2: stage 1: 8, stage 2: 12, stage 3: 30,
+# stage 4: 40, stage 5: 52 (plus 15 MUFU reciprocals, not counted here).
+ALGO_FP32_OPS_PER_PXCH = 142
+ALGO_MUFU_PER_PXCH = 15
+# Algorithmic HBM bytes per input pixel-channel: 1 read + 4 written (uint8).
+ALGO_BYTES_PER_PXCH = {"u8": 5, "f16": 10, "bf16": 10, "f32": 20}
+FP32_LANES_PER_SM = 128
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "zoom2x_fwd_1080p_u8.md")
+KERNEL_SOURCES = ["paper_2312_00229_gb300/csrc/wd_fwd_tile.cuh",
+                  "paper_2312_00229_gb300/csrc/wd_common.cuh",
+                  "paper_2312_00229_gb300/csrc/wd_fwd.cu"]
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10000)
+    ap.add_argument("--warmup", type=int, default=200)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--skip-extras", action="store_true",
+                    help="headline only (no fwd+bwd / batched / sweep / cascade)")
+    return ap.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d.get("hbm_gbs", 6800.0)), float(d.get("sm_max_mhz", 2070.0)), "measured"
+    return 6800.0, 2070.0, "fallback"
+
+
+def kernel_sha():
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source."""
+    if not os.path.exists(PROFILE_SUMMARY):
+        return None
+    text = open(PROFILE_SUMMARY).read()
+    m_sha = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
+    m_b = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not m_sha or not m_b or m_sha.group(1) != kernel_sha():
+        return None
+    return float(m_b.group(1))
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "20", "-f", self.path],
+                stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (one process per GPU; replicas, no data-path collective)
+# ---------------------------------------------------------------------------
+def dist_setup(n_gpus):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, value, device):
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (FP64) timing
+# ---------------------------------------------------------------------------
+def oracle_time_frames(frames: int, A01):
+    import oracle
+    t0 = time.perf_counter()
+    for _ in range(frames):
+        oracle.zoom2x(A01)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline_full_frames(A01, frames=3):
+    dt = oracle_time_frames(frames, A01)
+    return {"value": round(frames * OUT_PX / dt / 1e9, 6), "unit": "Gpix/s",
+            "cores": min(C, os.cpu_count() or 1), "kind": "oracle",
+            "sample": f"{frames} full 1920x1080x3 frames through the FP64 C oracle "
+                      f"(OpenMP over the 3 channel planes), {dt:.1f} s"}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import numpy as np
+    import oracle
+    from paper_2312_00229_gb300 import scenes
+    oracle.build()
+    img = scenes.piecewise_smooth(H, W, seed=scenes.seed_for(2))
+    A01 = scenes.planar(img).astype(np.float64) / 255.0
+    # Size each step's sample so that warm-up + timed steps fit in about two
+    # minutes.  A sample is a window of `rows` x `cols` input cells plus the
+    # method's footprint margins (4 cells before, 5 after); its output is
+    # 2 rows x 2 cols pixels.  Cost model: time per extended cell of the
+    # oracle's own grid (the window plus its 6 ghost cells per side).
+    probe_rows = 16
+    probe = A01[:, 500 - 4:500 + probe_rows + 5]
+    t0 = time.perf_counter()
+    oracle.zoom2x(probe)
+    t_probe = time.perf_counter() - t0
+    t_cell = t_probe / ((probe.shape[1] + 12) * (W + 12))
+    budget = 120.0 / max(1, args.steps + args.warmup)
+    rows = int(budget / (t_cell * (W + 12))) - 21
+    cols = W
+    if rows < 1:
+        rows = 1
+        cols = int(max(16, min(W - 9, budget / (t_cell * 22) - 21)))
+    rows = min(rows, H - 9)
+    r0 = max(4, min(200, H - 5 - rows))
+    c0 = 0 if cols == W else 4
+    sample = A01[:, r0 - 4:r0 + rows + 5, max(0, c0 - 4):c0 + cols + (5 if cols < W else 0)]
+    for _ in range(args.warmup):
+        oracle.zoom2x(sample)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.zoom2x(sample)
+    dt = time.perf_counter() - t0
+    out_px = args.steps * (2 * rows) * (2 * cols)
+    value = out_px / dt / 1e9
+    desc = (f"each step: output of input rows {r0}..{r0 + rows - 1} x {cols} columns x 3 "
+            f"channels of the 1920x1080 scene (window + 4/5-cell footprint margins), FP64 C "
+            f"oracle, OpenMP over the channel planes")
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "Gpix/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(dt / args.steps * 1e3, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "implementation": "FP64 CPU oracle"},
+            "cpu_baseline": {"value": round(value, 6), "unit": "Gpix/s",
+                             "cores": min(C, os.cpu_count() or 1), "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": round(value, 6), "unit": "Gpix/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU timing helpers
+# ---------------------------------------------------------------------------
+def time_graph(torch, fn_list, reps, warm=3):
+    """Captures fn_list (callables enqueuing work) into one graph, replays it
+    `reps` times, returns seconds per replay (CUDA events)."""
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        for _ in range(2):
+            for f in fn_list:
+                f()
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        for f in fn_list:
+            f()
+    for _ in range(warm):
+        g.replay()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        g.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3 / reps, g
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_2312_00229_gb300 import api, scenes
+    from paper_2312_00229_gb300 import build as cuda_build
+
+    world, rank, local = dist_setup(args.gpus)
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    cuda_build.build()
+    api.lib()
+    hbm_peak, sm_max_mhz, peak_kind = peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    alu_peak = sms * FP32_LANES_PER_SM * sm_max_mhz * 1e6  # FP32 ops/s
+
+    img = scenes.piecewise_smooth(H, W, seed=scenes.seed_for(2))
+    x_host = torch.from_numpy(scenes.planar(img))
+    R = 16
+    xs = [x_host.to(dev) for _ in range(R)]
+    outs = [torch.empty(C, 2 * H, 2 * W, dtype=torch.uint8, device=dev) for _ in range(R)]
+    params = api.Params()
+    fns = [lambda i=i: api.zoom2x_fwd(xs[i], params, out=outs[i]) for i in range(R)]
+
+    # warm-up (eager), then the graph of R launches
+    for i in range(max(args.warmup, 3)):
+        fns[i % R]()
+    torch.cuda.synchronize()
+    reps = max(1, -(-args.steps // R))
+    steps = reps * R
+    _, graph = time_graph(torch, fns, 1, warm=1)
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        graph.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = sampler.stop()
+    t_local = e0.elapsed_time(e1) / 1e3
+    t = max_over_ranks(world, t_local, dev)
+    value = world * steps * OUT_PX / t / 1e9
+    per_launch = t_local / steps
+
+    pxch = H * W * C
+    achieved_ops = ALGO_FP32_OPS_PER_PXCH * pxch / per_launch
+    achieved_gbs = ALGO_BYTES_PER_PXCH["u8"] * pxch / per_launch / 1e9
+    traffic = profiled_traffic()
+    roofline = {"bound": "alu", "achieved": round(achieved_ops / 1e12, 3),
+                "peak": round(alu_peak / 1e12, 3), "unit": "Top/s",
+                "frac": round(achieved_ops / alu_peak, 4), "traffic": traffic,
+                "kernel": "zoom2x_fwd_kernel<B2>",
+                "ops_per_pxch": ALGO_FP32_OPS_PER_PXCH,
+                "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_max_mhz:.0f} MHz",
+                "hbm": {"achieved": round(achieved_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+                        "frac": round(achieved_gbs / hbm_peak, 4), "peak_kind": peak_kind,
+                        "bytes_per_pxch": ALGO_BYTES_PER_PXCH["u8"],
+                        "frac_of_nominal_7900": round(achieved_gbs / 7900.0, 4)},
+                "avg_launch_us": round(per_launch * 1e6, 3)}
+
+    line = {"metric": METRIC, "value": round(value, 4), "unit": "Gpix/s", "n_gpus": world,
+            "steps": steps, "warmup": args.warmup, "ms_per_step": round(t / steps * 1e3, 5),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "storage": "u8", "out_mode": "2n x 2m",
+                       "beta": 2.0, "rows_per_band": 64, "strip_width": 240,
+                       "l2": "16 rotating input/output buffer sets (~500 MB) > 129 MB L2",
+                       "launch": "CUDA graph of 16 launches, replayed",
+                       "parallelism": f"replicas x{world} (no collective)"},
+            "roofline": roofline, "gpu_launches": steps, "clocks": clocks}
+
+    # ---- end to end through the public API with host buffers ---------------
+    x_pin = x_host.pin_memory()
+    o_pin = torch.empty(C, 2 * H, 2 * W, dtype=torch.uint8).pin_memory()
+    xd, od = xs[0], outs[0]
+
+    def e2e_step():
+        xd.copy_(x_pin, non_blocking=True)
+        api.zoom2x_fwd(xd, params, out=od)
+        o_pin.copy_(od, non_blocking=True)
+
+    for _ in range(3):
+        e2e_step()
+    torch.cuda.synchronize()
+    k_e2e = 50
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
+        e2e_step()
+    torch.cuda.synchronize()
+    t_e2e = max_over_ranks(world, time.perf_counter() - t0, dev)
+    line["e2e"] = {"value": round(world * k_e2e * OUT_PX / t_e2e / 1e9, 4), "unit": "Gpix/s",
+                   "h2d_bytes_per_step": int(x_host.numel()),
+                   "d2h_bytes_per_step": int(o_pin.numel()), "steps": k_e2e,
+                   "timer": "host wall clock, synchronized", "api": "api.zoom2x_fwd"}
+
+    if not args.skip_extras:
+        line.update(extras(torch, np, api, scenes, dev, world, hbm_peak))
+
+    if rank == 0:
+        A01 = scenes.planar(img).astype(np.float64) / 255.0
+        line["cpu_baseline"] = cpu_baseline_full_frames(A01)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def extras(torch, np, api, scenes, dev, world, hbm_peak):
+    out = {}
+    # fwd+bwd: 32x3x512x512 FP32, L2 loss against a 1024x1024 target
+    xb = np.stack([scenes.planar(scenes.piecewise_smooth(512, 512, scenes.seed_for(5, i),
+                                                         scale_features=True))
+                   for i in range(32)]).astype(np.float32) / 255.0
+    tgt = scenes.planar(scenes.piecewise_smooth(1024, 1024, scenes.seed_for(5, 999),
+                                                scale_features=True)).astype(np.float32) / 255.0
+    x = torch.from_numpy(xb).to(dev).requires_grad_(True)
+    T = torch.from_numpy(tgt).to(dev).expand(32, 3, 1024, 1024)
+
+    def step():
+        x.grad = None
+        y = api.zoom2x(x)
+        loss = (y - T).square().mean()
+        loss.backward()
+
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    k = 20
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(k):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    t_fb = e0.elapsed_time(e1) / 1e3 / k
+    with torch.no_grad():
+        xf = x.detach()
+        t_f, _ = time_graph(torch, [lambda: api.zoom2x_fwd(xf)], 20)
+    px = 32 * 1024 * 1024
+    out["fwd_bwd"] = {"value": round(world * px / t_fb / 1e9, 4), "unit": "Gpix/s",
+                      "ms_per_step": round(t_fb * 1e3, 3),
+                      "fwd_only_gpix_s": round(world * px / t_f / 1e9, 4),
+                      "workload": "32x3x512x512 FP32 -> 1024x1024, loss = mean((y - T)^2), "
+                                  "autograd step (forward + hand-written adjoint)"}
+    del x, T
+    torch.cuda.empty_cache()
+
+    # batched: 256 uneven images, FP16 storage, one persistent launch
+    imgs = scenes.uneven_batch(256)
+    xs = [torch.from_numpy(scenes.planar(im)).to(dev).float().div(255).half() for im in imgs]
+    plan = api.BatchedPlan(xs)
+    out_px = sum((2 * t.shape[1]) * (2 * t.shape[2]) for t in xs)
+    t_batched, _ = time_graph(torch, [plan.run], 20)
+    plain_outs = [torch.empty_like(o) for o in plan.outputs]
+    fns = [lambda i=i: api.zoom2x_fwd(xs[i], out=plain_outs[i]) for i in range(len(xs))]
+    t_plain, _ = time_graph(torch, fns, 20)
+    out["batched"] = {"value": round(world * out_px / t_batched / 1e9, 4), "unit": "Gpix/s",
+                      "plain_gpix_s": round(world * out_px / t_plain / 1e9, 4),
+                      "speedup_vs_plain": round(t_plain / t_batched, 3),
+                      "workload": "256 RGB images, sides uniform in [64, 1024], FP16 storage, "
+                                  "one persistent launch (graph replay) vs 256 launches "
+                                  "(graph replay)", "images": len(xs)}
+    del xs, plan, plain_outs
+    torch.cuda.empty_cache()
+
+    # storage-format sweep, 3840x2160x3 -> 7680x4320
+    big = scenes.planar(scenes.piecewise_smooth(2160, 3840, seed=scenes.seed_for(4)))
+    sweep = {}
+    pxch = 2160 * 3840 * 3
+    for name, dt in (("u8", torch.uint8), ("f16", torch.float16), ("bf16", torch.bfloat16),
+                     ("f32", torch.float32)):
+        if dt == torch.uint8:
+            xin = [torch.from_numpy(big).to(dev) for _ in range(2)]
+        else:
+            xin = [(torch.from_numpy(big).to(dev).float() / 255).to(dt) for _ in range(2)]
+        o = [torch.empty(3, 4320, 7680, dtype=dt, device=dev) for _ in range(2)]
+        t1, _ = time_graph(torch, [lambda i=i: api.zoom2x_fwd(xin[i], out=o[i]) for i in (0, 1)],
+                           25)
+        t1 /= 2
+        gbs = ALGO_BYTES_PER_PXCH[name] * pxch / t1 / 1e9
+        sweep[name] = {"gpix_s": round(world * 4320 * 7680 / t1 / 1e9, 4),
+                       "us": round(t1 * 1e6, 2), "hbm_gbs": round(gbs, 1),
+                       "hbm_frac": round(gbs / hbm_peak, 4)}
+        del xin, o
+        torch.cuda.empty_cache()
+    out["precision_sweep"] = {"workload": "3840x2160x3 -> 7680x4320x3, FP32 arithmetic",
+                              "formats": sweep}
+
+    # 8x cascade of a 512x512 pixel-art image (three 2x passes, FP32 between)
+    pa = torch.from_numpy(scenes.planar(scenes.pixel_art(512, 512, scenes.seed_for(4, 1)))).to(dev)
+    t8, _ = time_graph(torch, [lambda: api.cascade_zoom(pa, 3)], 20)
+    out["cascade8x"] = {"gpix_s": round(world * 4096 * 4096 / t8 / 1e9, 4),
+                        "us": round(t8 * 1e6, 1),
+                        "workload": "512x512x3 uint8 pixel art -> 4096x4096x3 uint8, "
+                                    "FP32 intermediates"}
+    return out
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

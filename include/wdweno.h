@@ -1,0 +1,156 @@
+/*
+ * wdweno.h -- C ABI of the GB300 (sm_103a) WD WENO 2x image zoom.
+ *
+ * The method is the two-phase "Weighted Direction" WENO interpolation of
+ * B. Crnkovic, J. Skific, T. Bosner, "WENO based adaptive image zooming
+ * algorithm" (arXiv 2312.00229), Sec. 3:
+ *   phase 1 (Sec. 3.1, Algorithm 1) fills the "x" points of the doubled grid
+ *   from four diagonal quadratic interpolants (Eq. p), weighted by
+ *   neighbour-smoothed smoothness indicators (Eqs. 2Dsmoothness,
+ *   2DsmoothnessFinal, alpha, IzrazOmega2d, 2dKombinacija);
+ *   phase 2 (Sec. 3.2, Algorithm 2) fills the "+" points the same way along
+ *   the axes, using the input samples and the phase-1 values (Eqs. tezine,
+ *   IzrazOmega2dRavno, 2dKombinacijaRavno).
+ * Each channel is processed independently.
+ *
+ * Conventions for every entry point
+ *   - All data pointers are DEVICE pointers owned by the caller.  The library
+ *     never allocates or frees device or host memory.
+ *   - Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
+ *     stream) and runs asynchronously; the call returns once it is enqueued.
+ *   - Sizes and strides are in ELEMENTS, not bytes; strides may be any
+ *     positive values (channel, row, column), so planar [C][H][W],
+ *     interleaved [H][W][C] and cropped views are all accepted.  The fastest
+ *     path is a unit column stride on the output with 4-element aligned rows.
+ *   - Arguments are validated on the host before anything is launched; a
+ *     failed check returns a negative WENO_E* code and enqueues nothing.
+ *     No device-side traps are used.
+ *   - Input and output must not overlap.
+ *   - The boundary rule (not given in the paper) is clamp-to-edge: the method
+ *     is evaluated on the edge-replicated extension of the image and cropped.
+ */
+#ifndef WDWENO_H
+#define WDWENO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define WENO_OK 0
+#define WENO_EINVAL -1     /* null pointer, bad size, stride, shape or overlap */
+#define WENO_EDTYPE -2     /* unsupported storage type combination */
+#define WENO_EWORKSPACE -3 /* workspace missing or too small */
+#define WENO_ECUDA -4      /* a CUDA call failed (launch or attribute query) */
+#define WENO_ERANGE -5     /* a size exceeds a documented maximum */
+
+/* Storage types.  Arithmetic is always FP32.  uint8 values are decoded as
+ * v / 255 and encoded as round-half-even(saturate(u) * 255). */
+typedef enum { WENO_U8 = 0, WENO_F16 = 1, WENO_BF16 = 2, WENO_F32 = 3 } weno_dtype;
+
+/* Output grid.  WENO_OUT_2N: 2n x 2m (every coarse cell owns a 2x2 quad;
+ * the last fine row/column is the scheme evaluated half a pixel past the
+ * edge, the domain of Theorem 1).  WENO_OUT_2N_MINUS_1: the (2n-1) x (2m-1)
+ * grid of Sec. 3, Fig. inputdata. */
+typedef enum { WENO_OUT_2N = 0, WENO_OUT_2N_MINUS_1 = 1 } weno_out_mode;
+
+/* Length scale of the smoothness indicator, Eq. (2Dsmoothness).
+ * NORMALIZED: the stencil's own node spacing in both phases, i.e. the 1-D
+ * indicator of Sec. 2 on each line: SI = g^2 + 13/12 s^2 with
+ * g = N1 - N0, s = N0 - 2 N1 + N2.  LITERAL_SQRT2H: sqrt(2) h as printed;
+ * on the axes of phase 2 this gives sqrt(2) (g^2 + 25/12 s^2). */
+typedef enum { WENO_SI_NORMALIZED = 0, WENO_SI_LITERAL_SQRT2H = 1 } weno_si_scale;
+
+typedef struct {
+  float beta;      /* exponent of Eq. (alpha); default 2 (Sec. 4); >= 0 */
+  float k_eps;     /* eps_h = k_eps * h^2 (Sec. 2); default 1e-8; >= 0 */
+  float h;         /* coarse grid spacing; default 1 (pixel units); > 0 */
+  int si_scale;    /* weno_si_scale; default WENO_SI_NORMALIZED */
+  int out_mode;    /* weno_out_mode; default WENO_OUT_2N */
+  int clamp_float; /* 1: saturate float outputs to [0, 1]; default 0.
+                      uint8 outputs always saturate. */
+} weno_params;
+
+/* One image: `channels` planes of height x width. */
+typedef struct {
+  void* data; /* device pointer, caller-owned */
+  int64_t height, width, channels;
+  int64_t stride_c, stride_h, stride_w; /* element strides, all > 0 */
+} weno_image;
+
+/* Defaults: beta 2, k_eps 1e-8, h 1, normalized SI, 2n x 2m, no clamp. */
+weno_params weno_params_default(void);
+
+/* Human-readable text of a status code (static storage). */
+const char* weno_status_string(int status);
+
+/* Forward 2x zoom, Sec. 3 (Algorithms 1 and 2).
+ *   in   : n x m x C image of type in_t (n, m, C >= 1)
+ *   out  : (2n x 2m or (2n-1) x (2m-1), per p->out_mode) x C, type out_t
+ *   p    : parameters (NULL = defaults)
+ * Any in_t/out_t pair from weno_dtype is accepted.
+ * Returns WENO_OK, WENO_EINVAL, WENO_EDTYPE or WENO_ECUDA. */
+int weno_zoom2x_fwd(const weno_image* in, weno_dtype in_t, const weno_image* out,
+                    weno_dtype out_t, const weno_params* p, void* stream);
+
+/* Adjoint (vector-Jacobian product) of weno_zoom2x_fwd with respect to its
+ * input, for FP32 data: grad_in = (d out / d in)^T grad_out, differentiating
+ * through the nonlinear weights (Eqs. alpha, IzrazOmega2d, IzrazOmega2dRavno),
+ * the neighbour-smoothed indicators (Eqs. 2DsmoothnessFinal, tezine), the
+ * indicators themselves (Eq. 2Dsmoothness), the interpolants (Eq. p), the
+ * phase-1 values that phase 2 reads, and the clamp-to-edge extension.
+ *   x         : the forward input (FP32, n x m x C)
+ *   grad_out  : FP32, shaped like the forward output for p->out_mode
+ *   grad_in   : FP32, shaped like x; overwritten (not accumulated)
+ *   workspace : device scratch of >= weno_zoom2x_bwd_workspace_bytes(x)
+ *               bytes, 16-byte aligned; no initialisation needed; it holds
+ *               the recomputed phase-1 values and per-point adjoints
+ * Returns WENO_OK, WENO_EINVAL, WENO_EWORKSPACE or WENO_ECUDA. */
+int weno_zoom2x_bwd(const weno_image* x, const weno_image* grad_out,
+                    const weno_image* grad_in, const weno_params* p, void* workspace,
+                    size_t workspace_bytes, void* stream);
+
+/* Scratch bytes weno_zoom2x_bwd needs for an input shaped like `x`
+ * (19 FP32 values per cell of the image extended by 6 cells per side, per
+ * channel).  Returns 0 for a malformed descriptor. */
+size_t weno_zoom2x_bwd_workspace_bytes(const weno_image* x);
+
+/* Workspace needed by weno_zoom2x_batched for `count` images (bytes). */
+size_t weno_zoom2x_batched_workspace_bytes(int count);
+
+/* Forward 2x zoom of `count` images of independent sizes in ONE persistent
+ * launch fed by a device-side tile queue.
+ *   d_in, d_out : DEVICE arrays of `count` weno_image descriptors (the
+ *                 descriptors, not just the pixels, live on the device, so
+ *                 the call can be captured into a CUDA graph and replayed)
+ *   workspace   : device buffer of >= weno_zoom2x_batched_workspace_bytes
+ *                 bytes; contents need no initialisation and are scratch
+ *   rows_per_tile, tile_width : tile shape (0 = library default); the
+ *                 autotuner chooses these per size class
+ * Shapes follow weno_zoom2x_fwd per image; descriptors are read on the
+ * device, so a malformed descriptor is skipped (its output is left
+ * untouched) rather than reported.
+ * Returns WENO_OK, WENO_EINVAL, WENO_EDTYPE, WENO_EWORKSPACE or WENO_ECUDA. */
+int weno_zoom2x_batched(int count, const weno_image* d_in, weno_dtype in_t,
+                        const weno_image* d_out, weno_dtype out_t, const weno_params* p,
+                        void* workspace, size_t workspace_bytes, int rows_per_tile,
+                        int tile_width, void* stream);
+
+/* weno_zoom2x_fwd with an explicit tile shape, for the autotuner.
+ *   rows_per_tile : coarse rows per CTA band, 1..4096 (0 = default 64)
+ *   tile_width    : coarse output columns per CTA; 0 or 240 (the built
+ *                   strip width, 128 threads owning two columns each)
+ * Returns as weno_zoom2x_fwd, or WENO_EINVAL for an unsupported shape and
+ * WENO_ERANGE when the band count exceeds 65535. */
+int weno_zoom2x_fwd_tiled(const weno_image* in, weno_dtype in_t, const weno_image* out,
+                          weno_dtype out_t, const weno_params* p, int rows_per_tile,
+                          int tile_width, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WDWENO_H */

@@ -1,0 +1,234 @@
+"""PyTorch-facing API of the WD WENO 2x zoom (arXiv 2312.00229, Sec. 3).
+
+PyTorch supplies device memory and streams; every step of the method runs in
+``libwdweno.so``.  Tensors must live on a CUDA device; there is no CPU path.
+
+Layouts: ``"chw"`` = [C, H, W] (also [N, C, H, W] and [H, W]), ``"hwc"`` =
+[H, W, C] (interleaved pixels).  Any strides are accepted.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+from typing import List, Optional, Sequence
+
+import torch
+
+from . import binding as B
+
+_DT = {torch.uint8: B.WENO_U8, torch.float16: B.WENO_F16, torch.bfloat16: B.WENO_BF16,
+       torch.float32: B.WENO_F32}
+
+
+@dataclasses.dataclass(frozen=True)
+class Params:
+    """Parameters of the method (``weno_params``).
+
+    beta  : exponent of Eq. (alpha) (Sec. 4 uses 2)
+    k_eps : eps_h = k_eps h^2 (Sec. 2: 1e-8)
+    h     : coarse grid spacing (1 = pixel units)
+    si_scale : 0 normalized indicator length scale, 1 literal sqrt(2) h
+    out_mode : 0 -> 2n x 2m output, 1 -> (2n-1) x (2m-1) (Sec. 3)
+    clamp_float : saturate float outputs to [0, 1]
+    """
+    beta: float = 2.0
+    k_eps: float = 1e-8
+    h: float = 1.0
+    si_scale: int = B.WENO_SI_NORMALIZED
+    out_mode: int = B.WENO_OUT_2N
+    clamp_float: bool = False
+
+    def c(self) -> B.weno_params:
+        p = B.weno_params()
+        p.beta, p.k_eps, p.h = float(self.beta), float(self.k_eps), float(self.h)
+        p.si_scale, p.out_mode, p.clamp_float = int(self.si_scale), int(self.out_mode), int(
+            bool(self.clamp_float))
+        return p
+
+
+def lib():
+    return B.load()
+
+
+def _stream(device) -> ctypes.c_void_p:
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _require_cuda(t: torch.Tensor, name: str):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor (the library has no CPU path)")
+    if t.dtype not in _DT:
+        raise TypeError(f"{name}: unsupported dtype {t.dtype}")
+
+
+def _planes(t: torch.Tensor, layout: str):
+    """(height, width, channels, stride_c, stride_h, stride_w) of a tensor,
+    folding a leading batch dimension into the channel count when the planes
+    are uniformly strided."""
+    if t.dim() == 2:
+        return t.shape[0], t.shape[1], 1, 1, t.stride(0), t.stride(1)
+    if layout == "hwc":
+        if t.dim() != 3:
+            raise ValueError("hwc layout needs a 3-D tensor [H, W, C]")
+        return t.shape[0], t.shape[1], t.shape[2], t.stride(2), t.stride(0), t.stride(1)
+    if t.dim() == 3:
+        return t.shape[1], t.shape[2], t.shape[0], t.stride(0), t.stride(1), t.stride(2)
+    if t.dim() == 4:
+        N, C = t.shape[0], t.shape[1]
+        if N == 1 or C == 1 or t.stride(0) == C * t.stride(1):
+            sc = t.stride(1) if C > 1 else t.stride(0)
+            return t.shape[2], t.shape[3], N * C, max(sc, 1), t.stride(2), t.stride(3)
+        raise ValueError("4-D input needs uniformly strided planes (e.g. contiguous NCHW)")
+    raise ValueError("expected a 2-D, 3-D or 4-D tensor")
+
+
+def image(t: torch.Tensor, layout: str = "chw") -> B.weno_image:
+    h, w, c, sc, sh, sw = _planes(t, layout)
+    im = B.weno_image()
+    im.data = t.data_ptr()
+    im.height, im.width, im.channels = int(h), int(w), int(c)
+    im.stride_c, im.stride_h, im.stride_w = int(max(sc, 1)), int(max(sh, 1)), int(max(sw, 1))
+    return im
+
+
+def out_hw(h: int, w: int, params: Params):
+    d = 1 if params.out_mode == B.WENO_OUT_2N_MINUS_1 else 0
+    return 2 * h - d, 2 * w - d
+
+
+def _out_like(x: torch.Tensor, params: Params, layout: str, dtype) -> torch.Tensor:
+    shape = list(x.shape)
+    if layout == "hwc":
+        shape[0], shape[1] = out_hw(shape[0], shape[1], params)
+    else:
+        shape[-2], shape[-1] = out_hw(shape[-2], shape[-1], params)
+    return torch.empty(shape, dtype=dtype, device=x.device)
+
+
+def zoom2x_fwd(x: torch.Tensor, params: Optional[Params] = None, out_dtype=None,
+               layout: str = "chw", rows_per_tile: int = 0,
+               out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """Forward 2x zoom (``weno_zoom2x_fwd``); no autograd."""
+    params = params or Params()
+    _require_cuda(x, "x")
+    if x.numel() == 0:
+        raise ValueError("empty input")
+    if out is None:
+        out = _out_like(x, params, layout, out_dtype or x.dtype)
+    _require_cuda(out, "out")
+    rc = B.weno_zoom2x_fwd_tiled(image(x, layout), _DT[x.dtype], image(out, layout),
+                                 _DT[out.dtype], params.c(), rows_per_tile, 0,
+                                 _stream(x.device))
+    B.check("weno_zoom2x_fwd", rc)
+    return out
+
+
+def zoom2x_bwd(x: torch.Tensor, grad_out: torch.Tensor, params: Optional[Params] = None,
+               layout: str = "chw", workspace: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """Input gradient of the zoom for FP32 data (``weno_zoom2x_bwd``)."""
+    params = params or Params()
+    _require_cuda(x, "x")
+    _require_cuda(grad_out, "grad_out")
+    if x.dtype != torch.float32 or grad_out.dtype != torch.float32:
+        raise TypeError("the adjoint runs on FP32 data")
+    grad_in = torch.empty_like(x)
+    xi = image(x, layout)
+    need = B.weno_zoom2x_bwd_workspace_bytes(xi)
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(need, dtype=torch.uint8, device=x.device)
+    rc = B.weno_zoom2x_bwd(xi, image(grad_out, layout), image(grad_in, layout), params.c(),
+                           ctypes.c_void_p(workspace.data_ptr()), need, _stream(x.device))
+    B.check("weno_zoom2x_bwd", rc)
+    return grad_in
+
+
+class WenoZoom2x(torch.autograd.Function):
+    """Differentiable WD WENO 2x zoom; backward is the hand-written adjoint."""
+
+    @staticmethod
+    def forward(ctx, x, params, layout):
+        ctx.params, ctx.layout = params, layout
+        ctx.save_for_backward(x)
+        return zoom2x_fwd(x, params, layout=layout)
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        (x,) = ctx.saved_tensors
+        g = zoom2x_bwd(x, grad_out.contiguous(), ctx.params, ctx.layout)
+        return g, None, None
+
+
+def zoom2x(x: torch.Tensor, params: Optional[Params] = None, out_dtype=None,
+           layout: str = "chw") -> torch.Tensor:
+    """2x zoom; differentiable for FP32 inputs that require grad."""
+    params = params or Params()
+    if torch.is_grad_enabled() and x.requires_grad:
+        if x.dtype != torch.float32 or (out_dtype not in (None, torch.float32)):
+            raise TypeError("gradients are supported for FP32 in and out")
+        return WenoZoom2x.apply(x, params, layout)
+    return zoom2x_fwd(x, params, out_dtype=out_dtype, layout=layout)
+
+
+def cascade_zoom(x: torch.Tensor, levels: int, params: Optional[Params] = None, out_dtype=None,
+                 inter_dtype=torch.float32, layout: str = "chw") -> torch.Tensor:
+    """``levels`` successive 2x zooms (Sec. 3.3, Eq. zoomfactor); the
+    intermediate images are kept in ``inter_dtype`` and only the last one is
+    encoded to ``out_dtype``."""
+    params = params or Params()
+    cur = x
+    for lvl in range(levels):
+        last = lvl == levels - 1
+        cur = zoom2x_fwd(cur, params, out_dtype=(out_dtype or x.dtype) if last else inter_dtype,
+                         layout=layout)
+    return cur
+
+
+class BatchedPlan:
+    """Device-resident descriptors, outputs and workspace of one batched call
+    (``weno_zoom2x_batched``).  ``run()`` enqueues the single persistent
+    launch; it can be captured into a CUDA graph and replayed."""
+
+    def __init__(self, images: Sequence[torch.Tensor], params: Optional[Params] = None,
+                 out_dtype=None, layout: str = "chw", rows_per_tile: int = 0,
+                 outputs: Optional[Sequence[torch.Tensor]] = None):
+        if len(images) == 0:
+            raise ValueError("empty batch")
+        self.params = params or Params()
+        self.layout = layout
+        self.rows_per_tile = int(rows_per_tile)
+        dev = images[0].device
+        in_dt = images[0].dtype
+        for im in images:
+            _require_cuda(im, "image")
+            if im.dtype != in_dt or im.device != dev:
+                raise ValueError("all images must share dtype and device")
+        self.inputs = list(images)
+        odt = out_dtype or in_dt
+        self.outputs = list(outputs) if outputs is not None else [
+            _out_like(im, self.params, layout, odt) for im in images]
+        self.in_t, self.out_t = _DT[in_dt], _DT[self.outputs[0].dtype]
+        n = len(images)
+        host_in = (B.weno_image * n)(*[image(t, layout) for t in self.inputs])
+        host_out = (B.weno_image * n)(*[image(t, layout) for t in self.outputs])
+        nbytes = ctypes.sizeof(B.weno_image) * n
+        self.d_in = torch.frombuffer(bytearray(bytes(host_in)), dtype=torch.uint8).to(dev)
+        self.d_out = torch.frombuffer(bytearray(bytes(host_out)), dtype=torch.uint8).to(dev)
+        assert self.d_in.numel() == nbytes
+        self.ws_bytes = B.weno_zoom2x_batched_workspace_bytes(n)
+        self.workspace = torch.empty(self.ws_bytes, dtype=torch.uint8, device=dev)
+        self.count = n
+        self.device = dev
+
+    def run(self) -> List[torch.Tensor]:
+        rc = B.weno_zoom2x_batched(self.count, ctypes.c_void_p(self.d_in.data_ptr()), self.in_t,
+                                   ctypes.c_void_p(self.d_out.data_ptr()), self.out_t,
+                                   self.params.c(), ctypes.c_void_p(self.workspace.data_ptr()),
+                                   self.ws_bytes, self.rows_per_tile, 0, _stream(self.device))
+        B.check("weno_zoom2x_batched", rc)
+        return self.outputs
+
+
+def zoom2x_batched(images: Sequence[torch.Tensor], params: Optional[Params] = None,
+                   out_dtype=None, layout: str = "chw", rows_per_tile: int = 0):
+    """Zooms images of independent sizes in one persistent launch."""
+    return BatchedPlan(images, params, out_dtype, layout, rows_per_tile).run()

@@ -1,0 +1,254 @@
+// C ABI of the WD WENO library (declarations and contracts: include/wdweno.h).
+// Host-side argument validation, folding of the method's constants, and
+// kernel dispatch.  Nothing here allocates memory.
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+
+#include "wd_bwd.h"
+#include "wd_batched.h"
+#include "wd_common.cuh"
+#include "wd_fwd.h"
+#include "wdweno.h"
+
+using namespace wdweno;
+
+namespace {
+
+constexpr int64_t kDefaultRowsPerBand = 64;
+
+int64_t dtype_size(int dt) {
+  switch (dt) {
+    case WENO_U8: return 1;
+    case WENO_F16: return 2;
+    case WENO_BF16: return 2;
+    case WENO_F32: return 4;
+    default: return 0;
+  }
+}
+
+bool image_ok(const weno_image* im) {
+  return im && im->data && im->height >= 1 && im->width >= 1 && im->channels >= 1 &&
+         im->stride_c >= 1 && im->stride_h >= 1 && im->stride_w >= 1 &&
+         im->height < (int64_t(1) << 31) && im->width < (int64_t(1) << 31) &&
+         im->channels < 65536;
+}
+
+// Byte range [lo, hi) touched by an image view.
+void byte_extent(const weno_image* im, int64_t esz, uintptr_t* lo, uintptr_t* hi) {
+  const uintptr_t base = reinterpret_cast<uintptr_t>(im->data);
+  const int64_t last = (im->channels - 1) * im->stride_c + (im->height - 1) * im->stride_h +
+                       (im->width - 1) * im->stride_w;
+  *lo = base;
+  *hi = base + static_cast<uintptr_t>((last + 1) * esz);
+}
+
+bool overlaps(const weno_image* a, int64_t ea, const weno_image* b, int64_t eb) {
+  uintptr_t alo, ahi, blo, bhi;
+  byte_extent(a, ea, &alo, &ahi);
+  byte_extent(b, eb, &blo, &bhi);
+  return alo < bhi && blo < ahi;
+}
+
+// Fold Eq. (alpha)'s eps_h and the neighbour weight of Eqs.
+// (2DsmoothnessFinal)/(tezine) into per-SI constants (see MethodConsts).
+bool fold_consts(const weno_params& p, MethodConsts* k, int* bmode) {
+  if (!(p.beta >= 0.f) || !(p.k_eps >= 0.f) || !(p.h > 0.f) || !std::isfinite(p.beta) ||
+      !std::isfinite(p.k_eps) || !std::isfinite(p.h))
+    return false;
+  if (p.si_scale != WENO_SI_NORMALIZED && p.si_scale != WENO_SI_LITERAL_SQRT2H) return false;
+  const double h = p.h;
+  const double w = h * h / 4.0;
+  const double eps_h = double(p.k_eps) * h * h;
+  const double spread = 1.0 + 4.0 * w;
+  k->w = float(w);
+  k->kappa1 = float(std::sqrt(13.0 / 12.0));
+  k->eps1 = float(eps_h / spread);
+  if (p.si_scale == WENO_SI_NORMALIZED) {
+    k->kappa2 = float(std::sqrt(13.0 / 12.0));
+    k->eps2 = float(eps_h / spread);
+  } else {
+    // sqrt(2) (g^2 + 25/12 s^2): the common sqrt(2) cancels in the weights
+    // once eps_h is divided by it.
+    k->kappa2 = float(std::sqrt(25.0 / 12.0));
+    k->eps2 = float(eps_h / (std::sqrt(2.0) * spread));
+  }
+  k->beta = p.beta;
+  k->clamp_float = p.clamp_float ? 1 : 0;
+  if (p.beta == 0.f) {
+    *bmode = B0;
+  } else if (p.beta == 2.f) {
+    *bmode = B2;
+  } else {
+    *bmode = BGEN;
+  }
+  return true;
+}
+
+int check_pair(const weno_image* in, int in_t, const weno_image* out, int out_t,
+               const weno_params& p, int64_t* orows, int64_t* ocols) {
+  if (!image_ok(in) || !image_ok(out)) return WENO_EINVAL;
+  if (dtype_size(in_t) == 0 || dtype_size(out_t) == 0) return WENO_EDTYPE;
+  if (p.out_mode != WENO_OUT_2N && p.out_mode != WENO_OUT_2N_MINUS_1) return WENO_EINVAL;
+  const bool m1 = p.out_mode == WENO_OUT_2N_MINUS_1;
+  *orows = 2 * in->height - (m1 ? 1 : 0);
+  *ocols = 2 * in->width - (m1 ? 1 : 0);
+  if (out->height != *orows || out->width != *ocols || out->channels != in->channels)
+    return WENO_EINVAL;
+  if (overlaps(in, dtype_size(in_t), out, dtype_size(out_t))) return WENO_EINVAL;
+  return WENO_OK;
+}
+
+FwdArgs make_fwd_args(const weno_image* in, int in_t, const weno_image* out, int out_t,
+                      int64_t orows, int64_t ocols, int64_t rows_per_band) {
+  FwdArgs a;
+  a.in = in->data;
+  a.out = out->data;
+  a.in_dtype = in_t;
+  a.out_dtype = out_t;
+  a.n = in->height;
+  a.m = in->width;
+  a.planes = in->channels;
+  a.in_sc = in->stride_c;
+  a.in_sh = in->stride_h;
+  a.in_sw = in->stride_w;
+  a.out_sc = out->stride_c;
+  a.out_sh = out->stride_h;
+  a.out_sw = out->stride_w;
+  a.orows = orows;
+  a.ocols = ocols;
+  a.rows_per_band = rows_per_band;
+  const int64_t esz = dtype_size(out_t);
+  const uintptr_t base = reinterpret_cast<uintptr_t>(out->data);
+  a.out_vec = (out->stride_w == 1) && (out->stride_h % 4 == 0) && (out->stride_c % 4 == 0) &&
+              (base % uintptr_t(4 * esz) == 0);
+  return a;
+}
+
+}  // namespace
+
+extern "C" {
+
+weno_params weno_params_default(void) {
+  weno_params p;
+  p.beta = 2.0f;
+  p.k_eps = 1e-8f;
+  p.h = 1.0f;
+  p.si_scale = WENO_SI_NORMALIZED;
+  p.out_mode = WENO_OUT_2N;
+  p.clamp_float = 0;
+  return p;
+}
+
+const char* weno_status_string(int status) {
+  switch (status) {
+    case WENO_OK: return "ok";
+    case WENO_EINVAL: return "invalid argument (pointer, size, stride, shape or overlap)";
+    case WENO_EDTYPE: return "unsupported storage type";
+    case WENO_EWORKSPACE: return "workspace missing or too small";
+    case WENO_ECUDA: return "CUDA launch or runtime error";
+    case WENO_ERANGE: return "size exceeds the documented maximum";
+    default: return "unknown status";
+  }
+}
+
+int weno_zoom2x_fwd_tiled(const weno_image* in, weno_dtype in_t, const weno_image* out,
+                          weno_dtype out_t, const weno_params* pp, int rows_per_tile,
+                          int tile_width, void* stream) {
+  const weno_params p = pp ? *pp : weno_params_default();
+  int64_t orows, ocols;
+  int rc = check_pair(in, in_t, out, out_t, p, &orows, &ocols);
+  if (rc != WENO_OK) return rc;
+  if (rows_per_tile < 0 || rows_per_tile > 4096) return WENO_EINVAL;
+  if (tile_width != 0 && tile_width != tile_width_fwd()) return WENO_EINVAL;
+  MethodConsts k;
+  int bmode;
+  if (!fold_consts(p, &k, &bmode)) return WENO_EINVAL;
+  const int64_t rpb = rows_per_tile > 0 ? rows_per_tile : kDefaultRowsPerBand;
+  FwdArgs a = make_fwd_args(in, in_t, out, out_t, orows, ocols, rpb);
+  if ((a.n + rpb - 1) / rpb > 65535) return WENO_ERANGE;
+  cudaError_t e = launch_zoom2x_fwd(a, k, bmode, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? WENO_OK : WENO_ECUDA;
+}
+
+int weno_zoom2x_fwd(const weno_image* in, weno_dtype in_t, const weno_image* out,
+                    weno_dtype out_t, const weno_params* p, void* stream) {
+  return weno_zoom2x_fwd_tiled(in, in_t, out, out_t, p, 0, 0, stream);
+}
+
+size_t weno_zoom2x_bwd_workspace_bytes(const weno_image* x) {
+  if (!x || x->height < 1 || x->width < 1 || x->channels < 1) return 0;
+  return bwd_workspace_bytes(x->height, x->width, x->channels);
+}
+
+int weno_zoom2x_bwd(const weno_image* x, const weno_image* grad_out, const weno_image* grad_in,
+                    const weno_params* pp, void* workspace, size_t workspace_bytes,
+                    void* stream) {
+  const weno_params p = pp ? *pp : weno_params_default();
+  int64_t orows, ocols;
+  int rc = check_pair(x, WENO_F32, grad_out, WENO_F32, p, &orows, &ocols);
+  if (rc != WENO_OK) return rc;
+  if (!image_ok(grad_in) || grad_in->height != x->height || grad_in->width != x->width ||
+      grad_in->channels != x->channels)
+    return WENO_EINVAL;
+  if (overlaps(grad_in, 4, x, 4) || overlaps(grad_in, 4, grad_out, 4)) return WENO_EINVAL;
+  if (!workspace || workspace_bytes < bwd_workspace_bytes(x->height, x->width, x->channels) ||
+      reinterpret_cast<uintptr_t>(workspace) % 16 != 0)
+    return WENO_EWORKSPACE;
+  if ((x->height + 2 * BWD_GHOST + 7) / 8 > 65535) return WENO_ERANGE;
+  MethodConsts k;
+  int bmode;
+  if (!fold_consts(p, &k, &bmode)) return WENO_EINVAL;
+  BwdArgs a;
+  a.x = static_cast<const float*>(x->data);
+  a.gout = static_cast<const float*>(grad_out->data);
+  a.gin = static_cast<float*>(grad_in->data);
+  a.n = x->height;
+  a.m = x->width;
+  a.planes = x->channels;
+  a.x_sc = x->stride_c; a.x_sh = x->stride_h; a.x_sw = x->stride_w;
+  a.g_sc = grad_out->stride_c; a.g_sh = grad_out->stride_h; a.g_sw = grad_out->stride_w;
+  a.gi_sc = grad_in->stride_c; a.gi_sh = grad_in->stride_h; a.gi_sw = grad_in->stride_w;
+  a.orows = orows;
+  a.ocols = ocols;
+  a.ws = static_cast<float*>(workspace);
+  cudaError_t e = launch_zoom2x_bwd(a, k, bmode, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? WENO_OK : WENO_ECUDA;
+}
+
+size_t weno_zoom2x_batched_workspace_bytes(int count) {
+  if (count < 0) return 0;
+  return batched_workspace_bytes(count);
+}
+
+int weno_zoom2x_batched(int count, const weno_image* d_in, weno_dtype in_t,
+                        const weno_image* d_out, weno_dtype out_t, const weno_params* pp,
+                        void* workspace, size_t workspace_bytes, int rows_per_tile,
+                        int tile_width, void* stream) {
+  const weno_params p = pp ? *pp : weno_params_default();
+  if (count < 0 || count > (1 << 24)) return WENO_EINVAL;
+  if (count == 0) return WENO_OK;
+  if (!d_in || !d_out) return WENO_EINVAL;
+  if (dtype_size(in_t) == 0 || dtype_size(out_t) == 0) return WENO_EDTYPE;
+  if (p.out_mode != WENO_OUT_2N && p.out_mode != WENO_OUT_2N_MINUS_1) return WENO_EINVAL;
+  if (!workspace || workspace_bytes < batched_workspace_bytes(count)) return WENO_EWORKSPACE;
+  if (reinterpret_cast<uintptr_t>(workspace) % 16 != 0) return WENO_EWORKSPACE;
+  if (rows_per_tile < 0 || rows_per_tile > 4096) return WENO_EINVAL;
+  if (tile_width != 0 && tile_width != tile_width_fwd()) return WENO_EINVAL;
+  MethodConsts k;
+  int bmode;
+  if (!fold_consts(p, &k, &bmode)) return WENO_EINVAL;
+  BatchedArgs a;
+  a.count = count;
+  a.in = d_in;
+  a.out = d_out;
+  a.in_dtype = in_t;
+  a.out_dtype = out_t;
+  a.out_mode = p.out_mode;
+  a.rows_per_band = rows_per_tile > 0 ? rows_per_tile : kDefaultRowsPerBand;
+  a.workspace = workspace;
+  cudaError_t e = launch_zoom2x_batched(a, k, bmode, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? WENO_OK : WENO_ECUDA;
+}
+
+}  // extern "C"

@@ -1,0 +1,172 @@
+// Batched forward 2x zoom: many images of independent sizes in one persistent
+// launch fed by a device-side tile queue.
+//
+// Workspace (caller-owned, no initialisation needed):
+//   [0]   unsigned long long  next tile (queue head)
+//   [8]   unsigned long long  total tiles
+//   [16]  unsigned long long  prefix[count + 1], exclusive prefix sum of the
+//                             tiles of each image (0 for a malformed one)
+// The setup kernel fills it from the device-resident descriptors, so a
+// stream capture of the call replays correctly with new pixel data.
+#include "wd_batched.h"
+#include "wd_fwd_tile.cuh"
+
+namespace wdweno {
+
+namespace {
+
+using fwd_tile::Exchange;
+using fwd_tile::THREADS;
+using fwd_tile::TILE_W;
+
+constexpr int SETUP_THREADS = 1024;
+
+struct Queue {
+  unsigned long long head;
+  unsigned long long total;
+  unsigned long long prefix[1];  // count + 1 entries
+};
+
+__device__ __forceinline__ int64_t dsize(int dt) { return dt == DT_U8 ? 1 : (dt == DT_F32 ? 4 : 2); }
+
+__device__ bool descriptor_ok(const weno_image& in, const weno_image& out, int out_mode) {
+  if (!in.data || !out.data) return false;
+  if (in.height < 1 || in.width < 1 || in.channels < 1 || in.channels >= 65536) return false;
+  if (in.height >= (int64_t(1) << 31) || in.width >= (int64_t(1) << 31)) return false;
+  if (in.stride_c < 1 || in.stride_h < 1 || in.stride_w < 1) return false;
+  if (out.stride_c < 1 || out.stride_h < 1 || out.stride_w < 1) return false;
+  const int64_t d = out_mode == WENO_OUT_2N_MINUS_1 ? 1 : 0;
+  return out.height == 2 * in.height - d && out.width == 2 * in.width - d &&
+         out.channels == in.channels;
+}
+
+__device__ unsigned long long image_tiles(const weno_image& in, int64_t rpb) {
+  const unsigned long long strips = (in.width + TILE_W - 1) / TILE_W;
+  const unsigned long long bands = (in.height + rpb - 1) / rpb;
+  return strips * bands * (unsigned long long)in.channels;
+}
+
+__global__ void __launch_bounds__(SETUP_THREADS) batched_setup_kernel(BatchedArgs a) {
+  Queue* q = static_cast<Queue*>(a.workspace);
+  __shared__ unsigned long long part[SETUP_THREADS];
+  const int t = threadIdx.x;
+  const int chunk = (a.count + SETUP_THREADS - 1) / SETUP_THREADS;
+  const int lo = min(a.count, t * chunk), hi = min(a.count, lo + chunk);
+  unsigned long long sum = 0;
+  for (int i = lo; i < hi; ++i) {
+    const weno_image in = a.in[i], out = a.out[i];
+    if (descriptor_ok(in, out, a.out_mode)) sum += image_tiles(in, a.rows_per_band);
+  }
+  part[t] = sum;
+  __syncthreads();
+  // Inclusive Hillis-Steele scan of the per-thread sums.
+  for (int off = 1; off < SETUP_THREADS; off <<= 1) {
+    unsigned long long v = t >= off ? part[t - off] : 0ULL;
+    __syncthreads();
+    part[t] += v;
+    __syncthreads();
+  }
+  unsigned long long run = part[t] - sum;  // exclusive start of this chunk
+  for (int i = lo; i < hi; ++i) {
+    q->prefix[i] = run;
+    const weno_image in = a.in[i], out = a.out[i];
+    if (descriptor_ok(in, out, a.out_mode)) run += image_tiles(in, a.rows_per_band);
+  }
+  if (t == SETUP_THREADS - 1) {
+    q->prefix[a.count] = part[t];
+    q->total = part[t];
+    q->head = 0ULL;
+  }
+}
+
+template <int BMODE>
+__global__ void __launch_bounds__(THREADS, 2) batched_fwd_kernel(BatchedArgs a, MethodConsts k) {
+  __shared__ Exchange ex;
+  __shared__ unsigned long long s_tile;
+  __shared__ int s_img;
+  Queue* q = static_cast<Queue*>(a.workspace);
+  const unsigned long long total = q->total;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const unsigned long long tile = atomicAdd(&q->head, 1ULL);
+      int img = -1;
+      if (tile < total) {
+        // largest i with prefix[i] <= tile < prefix[i + 1]
+        int lo = 0, hi = a.count - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (q->prefix[mid] <= tile) lo = mid; else hi = mid - 1;
+        }
+        img = lo;
+      }
+      s_tile = tile;
+      s_img = img;
+    }
+    __syncthreads();
+    const int img = s_img;
+    const unsigned long long tile = s_tile;
+    __syncthreads();  // s_tile / s_img are rewritten only after everyone read them
+    if (img < 0) break;
+    const weno_image in = a.in[img], out = a.out[img];
+    FwdArgs f;
+    f.in = in.data;
+    f.out = out.data;
+    f.in_dtype = a.in_dtype;
+    f.out_dtype = a.out_dtype;
+    f.n = in.height;
+    f.m = in.width;
+    f.planes = in.channels;
+    f.in_sc = in.stride_c; f.in_sh = in.stride_h; f.in_sw = in.stride_w;
+    f.out_sc = out.stride_c; f.out_sh = out.stride_h; f.out_sw = out.stride_w;
+    f.orows = out.height;
+    f.ocols = out.width;
+    f.rows_per_band = a.rows_per_band;
+    const uintptr_t base = reinterpret_cast<uintptr_t>(out.data);
+    f.out_vec = out.stride_w == 1 && out.stride_h % 4 == 0 && out.stride_c % 4 == 0 &&
+                base % uintptr_t(4 * dsize(a.out_dtype)) == 0;
+    const unsigned long long local = tile - q->prefix[img];
+    const unsigned long long strips = (f.m + TILE_W - 1) / TILE_W;
+    const unsigned long long bands = (f.n + f.rows_per_band - 1) / f.rows_per_band;
+    const unsigned long long per_plane = strips * bands;
+    const int64_t plane = (int64_t)(local / per_plane);
+    const unsigned long long rem = local % per_plane;
+    fwd_tile::zoom2x_fwd_tile<BMODE>(f, k, ex, (int64_t)(rem % strips), (int64_t)(rem / strips),
+                                     plane);
+  }
+}
+
+int persistent_grid(const void* kernel) {
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, THREADS, 0) != cudaSuccess)
+    return 0;
+  return sms * (per_sm > 0 ? per_sm : 1);
+}
+
+}  // namespace
+
+size_t batched_workspace_bytes(int count) {
+  size_t b = 16 + 8 * (size_t(count) + 1);
+  return (b + 15) & ~size_t(15);
+}
+
+cudaError_t launch_zoom2x_batched(const BatchedArgs& a, const MethodConsts& k, int bmode,
+                                  cudaStream_t stream) {
+  batched_setup_kernel<<<1, SETUP_THREADS, 0, stream>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const void* kern = bmode == B2 ? (const void*)batched_fwd_kernel<B2>
+                     : bmode == B0 ? (const void*)batched_fwd_kernel<B0>
+                                   : (const void*)batched_fwd_kernel<BGEN>;
+  const int grid = persistent_grid(kern);
+  if (grid <= 0) return cudaErrorInvalidValue;
+  switch (bmode) {
+    case B2: batched_fwd_kernel<B2><<<grid, THREADS, 0, stream>>>(a, k); break;
+    case B0: batched_fwd_kernel<B0><<<grid, THREADS, 0, stream>>>(a, k); break;
+    default: batched_fwd_kernel<BGEN><<<grid, THREADS, 0, stream>>>(a, k); break;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace wdweno

@@ -1,0 +1,28 @@
+// Internal launch interface of the forward kernel (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "wd_common.cuh"
+
+namespace wdweno {
+
+struct FwdArgs {
+  const void* in;
+  void* out;
+  int in_dtype, out_dtype;
+  int64_t n, m, planes;          // coarse rows, columns, channels
+  int64_t in_sc, in_sh, in_sw;   // element strides
+  int64_t out_sc, out_sh, out_sw;
+  int64_t orows, ocols;          // output extent (2n or 2n-1, ...)
+  int64_t rows_per_band;
+  int out_vec;                   // unit column stride and 4-element aligned rows
+};
+
+int tile_width_fwd();
+int threads_fwd();
+cudaError_t launch_zoom2x_fwd(const FwdArgs& a, const MethodConsts& k, int bmode,
+                              cudaStream_t stream);
+
+}  // namespace wdweno

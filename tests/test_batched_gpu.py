@@ -1,0 +1,105 @@
+"""Batched persistent launch: each image equals the single-image kernel bit
+for bit, CUDA-graph replay equals direct launches, malformed descriptors are
+skipped, and sampled windows match the oracle."""
+import numpy as np
+import pytest
+import torch
+
+import parity
+from paper_2312_00229_gb300 import api, scenes
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda"
+
+SIZES = [(1, 1), (1, 300), (300, 1), (64, 64), (65, 241), (500, 700), (97, 1024), (1024, 97),
+         (3, 5), (256, 480)]
+
+
+def _images(dtype=torch.uint8, sizes=SIZES, seed=0):
+    g = torch.Generator(device=DEV).manual_seed(seed)
+    imgs = []
+    for (h, w) in sizes:
+        t = torch.randint(0, 256, (3, h, w), device=DEV, generator=g, dtype=torch.uint8)
+        if dtype == torch.uint8:
+            imgs.append(t)
+        else:
+            imgs.append((t.float() / 255.0).to(dtype))
+    return imgs
+
+
+@pytest.mark.parametrize("dtype", [torch.uint8, torch.float16, torch.float32])
+@pytest.mark.parametrize("rows", [0, 16])
+def test_batched_equals_single(dtype, rows):
+    imgs = _images(dtype)
+    outs = api.zoom2x_batched(imgs, rows_per_tile=rows)
+    singles = [api.zoom2x_fwd(x, rows_per_tile=rows) for x in imgs]
+    torch.cuda.synchronize()
+    for o, s in zip(outs, singles):
+        assert torch.equal(o, s)
+
+
+def test_batched_out_mode_and_layout():
+    imgs = [x.permute(1, 2, 0).contiguous() for x in _images(torch.uint8, SIZES[:6], seed=3)]
+    prm = api.Params(out_mode=1)
+    outs = api.zoom2x_batched(imgs, prm, layout="hwc")
+    singles = [api.zoom2x_fwd(x, prm, layout="hwc") for x in imgs]
+    torch.cuda.synchronize()
+    for o, s in zip(outs, singles):
+        assert torch.equal(o, s)
+
+
+def test_batched_graph_replay():
+    imgs = _images(torch.float16, seed=5)
+    plan = api.BatchedPlan(imgs, out_dtype=torch.float16)
+    plan.run()  # warm-up outside capture
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(graph, stream=s):
+            plan.run()
+    torch.cuda.current_stream().wait_stream(s)
+    for seed in (11, 12):
+        new = _images(torch.float16, seed=seed)
+        for dst, src in zip(plan.inputs, new):
+            dst.copy_(src)
+        for o in plan.outputs:
+            o.zero_()
+        graph.replay()
+        torch.cuda.synchronize()
+        for x, o in zip(plan.inputs, plan.outputs):
+            assert torch.equal(o, api.zoom2x_fwd(x))
+
+
+def test_batched_skips_malformed_descriptor():
+    imgs = _images(torch.uint8, SIZES[:4], seed=8)
+    outs = [api._out_like(x, api.Params(), "chw", torch.uint8).fill_(77) for x in imgs]
+    bad = torch.full((3, 9, 9), 77, dtype=torch.uint8, device=DEV)  # wrong shape for image 1
+    outs[1] = bad
+    plan = api.BatchedPlan(imgs, outputs=outs)
+    plan.run()
+    torch.cuda.synchronize()
+    assert bool((bad == 77).all())
+    for i in (0, 2, 3):
+        assert torch.equal(outs[i], api.zoom2x_fwd(imgs[i]))
+
+
+def test_batched_uneven_scenes_against_oracle():
+    """A subset of the 256-image uneven workload (FP16 storage): all images
+    checked bit-exact against single launches, a few against the oracle."""
+    sizes = scenes.uneven_sizes()[:24]
+    imgs = scenes.uneven_batch(24)
+    xs = [torch.from_numpy(scenes.planar(im)).to(DEV).float().div(255).half() for im in imgs]
+    outs = api.zoom2x_batched(xs)
+    torch.cuda.synchronize()
+    for x, o in zip(xs, outs):
+        assert torch.equal(o, api.zoom2x_fwd(x))
+    for k in (0, 1, 5):
+        h, w = sizes[k]
+        A = parity.decode(xs[k][:, : min(h, 40), : min(w, 50)].cpu())
+        ref = parity.oracle_planes(A, api.Params())
+        hh, ww = min(h, 40) - 6, min(w, 50) - 6
+        if hh > 0 and ww > 0:
+            parity.compare(outs[k][:, : 2 * hh, : 2 * ww].cpu(), ref[:, : 2 * hh, : 2 * ww],
+                           "f16")

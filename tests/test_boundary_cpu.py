@@ -1,0 +1,150 @@
+"""C-ABI boundary checks that need no GPU: the library builds and loads,
+exports every entry point ``include/wdweno.h`` declares, and rejects bad
+arguments on the host before any launch."""
+import ctypes
+import os
+import re
+
+import pytest
+import torch
+
+from paper_2312_00229_gb300 import binding as B
+from paper_2312_00229_gb300 import api
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include",
+                      "wdweno.h")
+
+
+def _declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(weno_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declarations_match_binding():
+    assert _declared() == sorted(B.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol():
+    L = B.load()
+    for name in _declared():
+        assert hasattr(L, name), name
+        assert ctypes.cast(getattr(L, name), ctypes.c_void_p).value
+
+
+def test_params_default():
+    p = B.weno_params_default()
+    assert (p.beta, p.k_eps, p.h, p.si_scale, p.out_mode, p.clamp_float) == (
+        pytest.approx(2.0), pytest.approx(1e-8), pytest.approx(1.0), 0, 0, 0)
+
+
+def test_status_strings():
+    for st in (0, -1, -2, -3, -4, -5, -99):
+        assert isinstance(B.weno_status_string(st), str) and B.weno_status_string(st)
+
+
+def _img(ptr, h, w, c, sc=None, sh=None, sw=1):
+    im = B.weno_image()
+    im.data = ptr
+    im.height, im.width, im.channels = h, w, c
+    im.stride_w = sw
+    im.stride_h = sh if sh is not None else w * sw
+    im.stride_c = sc if sc is not None else h * im.stride_h
+    return im
+
+
+FAKE_IN = 0x10000000
+FAKE_OUT = 0x20000000
+
+
+def test_fwd_rejects_bad_arguments_without_launching():
+    p = B.weno_params_default()
+    good_in = _img(FAKE_IN, 4, 5, 3)
+    good_out = _img(FAKE_OUT, 8, 10, 3)
+    cases = [
+        (_img(0, 4, 5, 3), good_out, B.WENO_U8, B.WENO_U8, B.WENO_EINVAL),        # null
+        (_img(FAKE_IN, 0, 5, 3), good_out, B.WENO_U8, B.WENO_U8, B.WENO_EINVAL),  # empty
+        (_img(FAKE_IN, 4, 5, 3, sw=0), good_out, B.WENO_U8, B.WENO_U8, B.WENO_EINVAL),
+        (good_in, _img(FAKE_OUT, 8, 9, 3), B.WENO_U8, B.WENO_U8, B.WENO_EINVAL),  # shape
+        (good_in, _img(FAKE_OUT, 8, 10, 2), B.WENO_U8, B.WENO_U8, B.WENO_EINVAL),  # channels
+        (good_in, good_out, 7, B.WENO_U8, B.WENO_EDTYPE),
+        (good_in, good_out, B.WENO_U8, -1, B.WENO_EDTYPE),
+        (good_in, _img(FAKE_IN + 10, 8, 10, 3), B.WENO_U8, B.WENO_U8, B.WENO_EINVAL),  # overlap
+    ]
+    for i, (a, b, ta, tb, want) in enumerate(cases):
+        assert B.weno_zoom2x_fwd(a, ta, b, tb, p, None) == want, i
+    bad = B.weno_params_default()
+    bad.h = 0.0
+    assert B.weno_zoom2x_fwd(good_in, 0, good_out, 0, bad, None) == B.WENO_EINVAL
+    bad = B.weno_params_default()
+    bad.beta = -1.0
+    assert B.weno_zoom2x_fwd(good_in, 0, good_out, 0, bad, None) == B.WENO_EINVAL
+    bad = B.weno_params_default()
+    bad.out_mode = 5
+    assert B.weno_zoom2x_fwd(good_in, 0, good_out, 0, bad, None) == B.WENO_EINVAL
+    # (2n-1) mode changes the expected output shape
+    m1 = B.weno_params_default()
+    m1.out_mode = 1
+    assert B.weno_zoom2x_fwd(good_in, 0, good_out, 0, m1, None) == B.WENO_EINVAL
+    # unsupported tile shapes
+    assert B.weno_zoom2x_fwd_tiled(good_in, 0, good_out, 0, p, -1, 0, None) == B.WENO_EINVAL
+    assert B.weno_zoom2x_fwd_tiled(good_in, 0, good_out, 0, p, 0, 100, None) == B.WENO_EINVAL
+
+
+def test_bwd_rejects_bad_arguments_without_launching():
+    p = B.weno_params_default()
+    x = _img(FAKE_IN, 4, 5, 1)
+    go = _img(FAKE_OUT, 8, 10, 1)
+    gi = _img(0x30000000, 4, 5, 1)
+    need = B.weno_zoom2x_bwd_workspace_bytes(x)
+    assert need == 4 * 19 * (4 + 12) * (5 + 12)
+    assert B.weno_zoom2x_bwd(x, go, gi, p, None, need, None) == B.WENO_EWORKSPACE
+    assert B.weno_zoom2x_bwd(x, go, gi, p, 0x40000000, need - 1, None) == B.WENO_EWORKSPACE
+    assert B.weno_zoom2x_bwd(x, go, gi, p, 0x40000004, need, None) == B.WENO_EWORKSPACE
+    assert B.weno_zoom2x_bwd(x, go, _img(0x30000000, 4, 4, 1), p, 0x40000000, need,
+                             None) == B.WENO_EINVAL
+    assert B.weno_zoom2x_bwd(x, go, _img(FAKE_IN, 4, 5, 1), p, 0x40000000, need,
+                             None) == B.WENO_EINVAL  # grad_in aliases x
+    assert B.weno_zoom2x_bwd_workspace_bytes(_img(FAKE_IN, 0, 5, 1)) == 0
+
+
+def test_batched_rejects_bad_arguments_without_launching():
+    p = B.weno_params_default()
+    need = B.weno_zoom2x_batched_workspace_bytes(3)
+    assert need >= 16 + 8 * 4 and need % 16 == 0
+    assert B.weno_zoom2x_batched(0, None, 0, None, 0, p, None, 0, 0, 0, None) == B.WENO_OK
+    assert B.weno_zoom2x_batched(-1, 1, 0, 1, 0, p, 2, need, 0, 0, None) == B.WENO_EINVAL
+    assert B.weno_zoom2x_batched(3, None, 0, 1, 0, p, 2, need, 0, 0, None) == B.WENO_EINVAL
+    assert B.weno_zoom2x_batched(3, 1, 9, 1, 0, p, 2, need, 0, 0, None) == B.WENO_EDTYPE
+    assert B.weno_zoom2x_batched(3, 1, 0, 1, 0, p, None, need, 0, 0, None) == B.WENO_EWORKSPACE
+    assert B.weno_zoom2x_batched(3, 1, 0, 1, 0, p, 0x100, need - 16, 0, 0,
+                                 None) == B.WENO_EWORKSPACE
+    assert B.weno_zoom2x_batched(3, 1, 0, 1, 0, p, 0x100, need, 0, 77, None) == B.WENO_EINVAL
+
+
+def test_descriptor_folding_on_host_tensors():
+    """Descriptor construction (pure host logic) for the layouts the API takes."""
+    x = torch.zeros(3, 7, 9)
+    im = api.image(x)
+    assert (im.height, im.width, im.channels, im.stride_c, im.stride_h, im.stride_w) == (
+        7, 9, 3, 63, 9, 1)
+    x = torch.zeros(7, 9, 4)
+    im = api.image(x, "hwc")
+    assert (im.height, im.width, im.channels, im.stride_c, im.stride_h, im.stride_w) == (
+        7, 9, 4, 1, 36, 4)
+    x = torch.zeros(5, 3, 7, 9)
+    im = api.image(x)
+    assert (im.height, im.width, im.channels, im.stride_c) == (7, 9, 15, 63)
+    x = torch.zeros(3, 20, 30)[:, 2:9, 5:14]  # cropped view
+    im = api.image(x)
+    assert (im.height, im.width, im.channels, im.stride_c, im.stride_h, im.stride_w) == (
+        7, 9, 3, 600, 30, 1)
+    with pytest.raises(ValueError):
+        api.image(torch.zeros(4, 3, 8, 8).transpose(0, 1))
+    assert api.out_hw(7, 9, api.Params()) == (14, 18)
+    assert api.out_hw(7, 9, api.Params(out_mode=1)) == (13, 17)
+
+
+def test_api_refuses_cpu_tensors():
+    with pytest.raises(ValueError):
+        api.zoom2x_fwd(torch.zeros(1, 4, 4))

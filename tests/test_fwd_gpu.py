@@ -1,0 +1,184 @@
+"""Forward parity: CUDA path (through the C ABI) against the FP64 oracle."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import parity
+from paper_2312_00229_gb300 import api, scenes
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda"
+RNG = np.random.default_rng(20231201)
+
+
+def _run(A01: np.ndarray, in_dt: str, out_dt: str, params=api.Params(), layout="chw",
+         rows_per_tile=0):
+    """A01: float planes [C, H, W] in [0, 1] (or any range for f32)."""
+    x = parity.encode(A01, in_dt)
+    if layout == "hwc":
+        x = x.permute(1, 2, 0).contiguous()
+    xd = x.to(DEV)
+    out = api.zoom2x_fwd(xd, params, out_dtype=parity.TORCH_DT[out_dt], layout=layout,
+                         rows_per_tile=rows_per_tile)
+    torch.cuda.synchronize()
+    if layout == "hwc":
+        out = out.permute(2, 0, 1)
+        x = x.permute(2, 0, 1)
+    ref = parity.oracle_planes(parity.decode(x), params)
+    return out, ref
+
+
+SHAPES = [(1, 1), (1, 17), (23, 1), (2, 3), (5, 7), (64, 64), (65, 241), (130, 481),
+          (33, 500), (7, 719)]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("mode", [0, 1])
+def test_fwd_f32_random_sizes(shape, mode):
+    A = RNG.random((2,) + shape)
+    out, ref = _run(A, "f32", "f32", api.Params(out_mode=mode))
+    parity.compare(out, ref, "f32")
+
+
+DTS = ["u8", "f16", "bf16", "f32"]
+
+
+@pytest.mark.parametrize("in_dt", DTS)
+@pytest.mark.parametrize("out_dt", DTS)
+def test_fwd_storage_types(in_dt, out_dt):
+    img = scenes.piecewise_smooth(37, 300, seed=scenes.seed_for(4, 7), scale_features=True)
+    A = scenes.planar(img).astype(np.float64) / 255.0
+    out, ref = _run(A, in_dt, out_dt)
+    parity.compare(out, ref, out_dt)
+
+
+@pytest.mark.parametrize("beta", [0.0, 1.0, 1.5, 3.0])
+def test_fwd_beta(beta):
+    A = RNG.random((1, 40, 250))
+    out, ref = _run(A, "f32", "f32", api.Params(beta=beta))
+    parity.compare(out, ref, "f32")
+
+
+def test_fwd_literal_si_scale_and_h():
+    A = RNG.random((1, 29, 243))
+    for prm in (api.Params(si_scale=1), api.Params(h=1 / 64), api.Params(h=0.37, si_scale=1),
+                api.Params(k_eps=1e-4), api.Params(k_eps=0.0, h=0.5)):
+        out, ref = _run(A, "f32", "f32", prm)
+        parity.compare(out, ref, "f32")
+
+
+def test_fwd_clamp_float():
+    A = scenes.planar(scenes.pixel_art(48, 260, scenes.seed_for(4, 3))) / 255.0
+    out, ref = _run(A, "u8", "f32", api.Params(clamp_float=True))
+    parity.compare(out, ref, "f32", clamp_float=True)
+
+
+def test_fwd_analytic_step_64():
+    """64x64 sin(2 pi x) cos(3 pi y) + step, h = 1/64 (pixel centres)."""
+    A = scenes.analytic_step(64)[None]
+    for mode in (0, 1):
+        out, ref = _run(A, "f32", "f32", api.Params(h=1 / 64, out_mode=mode))
+        parity.compare(out, ref, "f32", value_range=float(A.max() - A.min()))
+
+
+@pytest.mark.parametrize("layout", ["hwc"])
+def test_fwd_interleaved_layout(layout):
+    img = scenes.piecewise_smooth(41, 333, seed=scenes.seed_for(2, 5), scale_features=True)
+    A = scenes.planar(img) / 255.0
+    out, ref = _run(A, "u8", "u8", layout=layout)
+    parity.compare(out, ref, "u8")
+
+
+def test_fwd_strided_views_and_batch():
+    base = torch.rand(3, 90, 700, device=DEV)
+    view = base[:, 5:77, 11:612]  # cropped, non-contiguous rows
+    out_full = torch.zeros(3, 200, 1400, device=DEV)
+    out_view = out_full[:, 3:147, 7:1209]
+    api.zoom2x_fwd(view, out=out_view)
+    torch.cuda.synchronize()
+    ref = parity.oracle_planes(view.double().cpu().numpy(), api.Params())
+    parity.compare(out_view, ref, "f32")
+    # untouched margin stays zero
+    assert float(out_full[:, :3].abs().max()) == 0.0
+    assert float(out_full[:, :, :7].abs().max()) == 0.0
+    # NCHW batch folds into planes
+    xb = torch.rand(4, 2, 19, 250, device=DEV)
+    ob = api.zoom2x_fwd(xb)
+    torch.cuda.synchronize()
+    refb = parity.oracle_planes(xb.double().cpu().numpy(), api.Params())
+    parity.compare(ob, refb, "f32")
+
+
+def test_fwd_tile_shape_invariance():
+    """Every value is formed by the same arithmetic whatever the band height,
+    so outputs are bit-identical across tile shapes."""
+    x = torch.rand(2, 301, 517, device=DEV)
+    outs = [api.zoom2x_fwd(x, rows_per_tile=r) for r in (0, 1, 7, 64, 100, 400)]
+    torch.cuda.synchronize()
+    for o in outs[1:]:
+        assert torch.equal(o, outs[0])
+
+
+def _windows(H, W, count, size=(24, 40), margin=6):
+    wins = [(0, 0), (0, W - size[1]), (H - size[0], 0), (H - size[0], W - size[1])]
+    for _ in range(count):
+        wins.append((int(RNG.integers(0, H - size[0] + 1)), int(RNG.integers(0, W - size[1] + 1))))
+    return wins
+
+
+def _check_windows(A01, out_gpu, dt, params, wins, size=(24, 40), margin=6):
+    """Oracle on input crops with a margin: output quads whose footprint
+    (-4..+5 input cells) stays inside the crop equal the full-image result;
+    at the image border the crop reaches the border, so clamping agrees."""
+    C, H, W = A01.shape
+    ties = 0
+    for (r0, c0) in wins:
+        ra, rb = max(0, r0 - margin), min(H, r0 + size[0] + margin)
+        ca, cb = max(0, c0 - margin), min(W, c0 + size[1] + margin)
+        ref = parity.oracle_planes(A01[:, ra:rb, ca:cb], params)
+        pr, pc = 2 * (r0 - ra), 2 * (c0 - ca)
+        ref = ref[:, pr:pr + 2 * size[0], pc:pc + 2 * size[1]]
+        g = out_gpu[:, 2 * r0:2 * r0 + 2 * size[0], 2 * c0:2 * c0 + 2 * size[1]]
+        ties += parity.compare(g, ref, dt)[1]
+    return ties
+
+
+def test_fwd_full_hd_rgb_u8_sampled():
+    """1920x1080 RGB uint8 piecewise-smooth scene -> 3840x2160, launched as
+    the benchmark launches it; the oracle checks sampled windows (corners
+    included)."""
+    img = scenes.piecewise_smooth(1080, 1920, seed=scenes.seed_for(2))
+    x = torch.from_numpy(scenes.planar(img)).to(DEV)
+    out = api.zoom2x_fwd(x).cpu()
+    A01 = scenes.planar(img).astype(np.float64) / 255.0
+    ties = _check_windows(A01, out, "u8", api.Params(), _windows(1080, 1920, 12))
+    assert ties < 20
+
+
+def test_fwd_4k_precision_sweep_sampled():
+    """3840x2160 RGB scene stored as uint8 / FP16 / BF16 / FP32 -> 7680x4320."""
+    img = scenes.piecewise_smooth(2160, 3840, seed=scenes.seed_for(4))
+    A01 = scenes.planar(img).astype(np.float64) / 255.0
+    wins = _windows(2160, 3840, 4)
+    for dt in ("u8", "f16", "bf16", "f32"):
+        x = parity.encode(A01, dt).to(DEV)
+        out = api.zoom2x_fwd(x).cpu()
+        _check_windows(parity.decode(x.cpu()), out, dt, api.Params(), wins)
+
+
+def test_fwd_large_planes_64bit_offsets():
+    """3 x 16384 x 16384 uint8 input: output offsets exceed 2^31."""
+    n = 16384
+    x = torch.empty(3, n, n, dtype=torch.uint8, device=DEV)
+    g = torch.Generator(device=DEV).manual_seed(7)
+    x.copy_(torch.randint(0, 256, (3, n, n), device=DEV, generator=g, dtype=torch.uint8))
+    out = api.zoom2x_fwd(x)
+    torch.cuda.synchronize()
+    A01 = x[:, -40:, -60:].cpu().numpy().astype(np.float64) / 255.0
+    ref = parity.oracle_planes(A01, api.Params())
+    # bottom-right corner of the last plane: the largest output offsets
+    parity.compare(out[:, -2 * 30:, -2 * 50:].cpu(), ref[:, -60:, -100:], "u8")
+    del out, x
+    torch.cuda.empty_cache()
