@@ -149,6 +149,30 @@ int weno_zoom2x_fwd_tiled(const weno_image* in, weno_dtype in_t, const weno_imag
                           weno_dtype out_t, const weno_params* p, int rows_per_tile,
                           int tile_width, void* stream);
 
+/* weno_zoom2x_batched without a workspace, for callers that cannot allocate
+ * device memory (for example code inside another application's real-time
+ * video pipeline, where cudaMalloc may synchronise the device and stall every
+ * other stream, or a plugin that is given image pointers but no allocator).
+ * The paper has no counterpart: this is a deployment variant of the batched
+ * call, with the same arguments minus the workspace.
+ *   - The tile queue lives in a fixed array inside the library's own device
+ *     memory (WENO_NOALLOC_SCRATCH_BYTES bytes, held on every GPU that loads
+ *     the library until the process exits); at most WENO_NOALLOC_MAX_IMAGES
+ *     images per call, larger counts return WENO_ERANGE.
+ *   - The first call on a device looks up the array's device address with
+ *     cudaGetSymbolAddress (that device must be current); make that first
+ *     call before any stream capture.
+ *   - The call allocates nothing (no cudaMalloc, cudaFree or allocating
+ *     library routine).  Every call shares the one array and resets what it
+ *     uses, so calls that overlap on the GPU (e.g. on two streams at once)
+ *     race and must be serialised by the caller.
+ * Returns as weno_zoom2x_batched, plus WENO_ERANGE. */
+#define WENO_NOALLOC_MAX_IMAGES 4096
+#define WENO_NOALLOC_SCRATCH_BYTES 32800
+int weno_zoom2x_batched_noalloc(int count, const weno_image* d_in, weno_dtype in_t,
+                                const weno_image* d_out, weno_dtype out_t, const weno_params* p,
+                                int rows_per_tile, int tile_width, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

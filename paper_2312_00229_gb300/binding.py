@@ -27,7 +27,9 @@ EXPORTS = (
     "weno_zoom2x_bwd_workspace_bytes",
     "weno_zoom2x_batched_workspace_bytes",
     "weno_zoom2x_batched",
+    "weno_zoom2x_batched_noalloc",
 )
+WENO_NOALLOC_MAX_IMAGES = 4096
 
 
 class weno_params(ctypes.Structure):
@@ -69,6 +71,8 @@ _SIGS = {
     "weno_zoom2x_batched_workspace_bytes": ([ctypes.c_int], ctypes.c_size_t),
     "weno_zoom2x_batched": ([ctypes.c_int, _VP, ctypes.c_int, _VP, ctypes.c_int, _PRM, _VP,
                              ctypes.c_size_t, ctypes.c_int, ctypes.c_int, _VP], ctypes.c_int),
+    "weno_zoom2x_batched_noalloc": ([ctypes.c_int, _VP, ctypes.c_int, _VP, ctypes.c_int, _PRM,
+                                     ctypes.c_int, ctypes.c_int, _VP], ctypes.c_int),
 }
 
 _lock = threading.Lock()
@@ -149,3 +153,10 @@ def weno_zoom2x_batched(count, d_in, in_t, d_out, out_t, params, workspace, work
                                       ctypes.byref(params) if params is not None else None,
                                       workspace, int(workspace_bytes), int(rows_per_tile),
                                       int(tile_width), stream)
+
+
+def weno_zoom2x_batched_noalloc(count, d_in, in_t, d_out, out_t, params, rows_per_tile,
+                                tile_width, stream) -> int:
+    return load().weno_zoom2x_batched_noalloc(int(count), d_in, in_t, d_out, out_t,
+                                              ctypes.byref(params) if params is not None else None,
+                                              int(rows_per_tile), int(tile_width), stream)

@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libwdweno.so")
-SOURCES = ["wd_api.cu", "wd_fwd.cu", "wd_batched.cu", "wd_bwd.cu"]
+SOURCES = ["wd_api.cu", "wd_fwd.cu", "wd_batched.cu", "wd_bwd.cu", "wd_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
