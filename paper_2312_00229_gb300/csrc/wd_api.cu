@@ -120,8 +120,8 @@ FwdArgs make_fwd_args(const weno_image* in, int in_t, const weno_image* out, int
   a.rows_per_band = rows_per_band;
   const int64_t esz = dtype_size(out_t);
   const uintptr_t base = reinterpret_cast<uintptr_t>(out->data);
-  a.out_vec = (out->stride_w == 1) && (out->stride_h % 4 == 0) && (out->stride_c % 4 == 0) &&
-              (base % uintptr_t(4 * esz) == 0);
+  a.out_vec = (out->stride_w == 1) && (out->stride_h % 2 == 0) && (out->stride_c % 2 == 0) &&
+              (base % uintptr_t(2 * esz) == 0);
   return a;
 }
 

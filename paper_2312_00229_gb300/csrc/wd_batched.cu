@@ -9,7 +9,7 @@
 // The setup kernel fills it from the device-resident descriptors, so a
 // stream capture of the call replays correctly with new pixel data.
 #include "wd_batched.h"
-#include "wd_fwd_tile.cuh"
+#include "wd_fwd_kernels.cuh"
 
 namespace wdweno {
 
@@ -79,8 +79,9 @@ __global__ void __launch_bounds__(SETUP_THREADS) batched_setup_kernel(BatchedArg
   }
 }
 
-template <int BMODE>
-__global__ void __launch_bounds__(THREADS, 2) batched_fwd_kernel(BatchedArgs a, MethodConsts k) {
+template <int BMODE, class IO>
+__global__ void __launch_bounds__(THREADS, WDWENO_FWD_MIN_BLOCKS)
+    batched_fwd_kernel(BatchedArgs a, MethodConsts k) {
   __shared__ Exchange ex;
   __shared__ unsigned long long s_tile;
   __shared__ int s_img;
@@ -122,16 +123,16 @@ __global__ void __launch_bounds__(THREADS, 2) batched_fwd_kernel(BatchedArgs a, 
     f.ocols = out.width;
     f.rows_per_band = a.rows_per_band;
     const uintptr_t base = reinterpret_cast<uintptr_t>(out.data);
-    f.out_vec = out.stride_w == 1 && out.stride_h % 4 == 0 && out.stride_c % 4 == 0 &&
-                base % uintptr_t(4 * dsize(a.out_dtype)) == 0;
+    f.out_vec = out.stride_w == 1 && out.stride_h % 2 == 0 && out.stride_c % 2 == 0 &&
+                base % uintptr_t(2 * dsize(a.out_dtype)) == 0;
     const unsigned long long local = tile - q->prefix[img];
     const unsigned long long strips = (f.m + TILE_W - 1) / TILE_W;
     const unsigned long long bands = (f.n + f.rows_per_band - 1) / f.rows_per_band;
     const unsigned long long per_plane = strips * bands;
     const int64_t plane = (int64_t)(local / per_plane);
     const unsigned long long rem = local % per_plane;
-    fwd_tile::zoom2x_fwd_tile<BMODE>(f, k, ex, (int64_t)(rem % strips), (int64_t)(rem / strips),
-                                     plane);
+    fwd_tile::zoom2x_fwd_tile<BMODE, IO>(f, k, ex, (int64_t)(rem % strips),
+                                         (int64_t)(rem / strips), plane);
   }
 }
 
@@ -151,22 +152,33 @@ size_t batched_workspace_bytes(int count) {
   return (b + 15) & ~size_t(15);
 }
 
+template <int BMODE, class IO>
+cudaError_t launch_persistent(const BatchedArgs& a, const MethodConsts& k, cudaStream_t stream) {
+  const int grid = persistent_grid((const void*)batched_fwd_kernel<BMODE, IO>);
+  if (grid <= 0) return cudaErrorInvalidValue;
+  batched_fwd_kernel<BMODE, IO><<<grid, THREADS, 0, stream>>>(a, k);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_zoom2x_batched(const BatchedArgs& a, const MethodConsts& k, int bmode,
                                   cudaStream_t stream) {
+  using fwd_tile::DynIO;
+  using fwd_tile::TypedIO;
   batched_setup_kernel<<<1, SETUP_THREADS, 0, stream>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const void* kern = bmode == B2 ? (const void*)batched_fwd_kernel<B2>
-                     : bmode == B0 ? (const void*)batched_fwd_kernel<B0>
-                                   : (const void*)batched_fwd_kernel<BGEN>;
-  const int grid = persistent_grid(kern);
-  if (grid <= 0) return cudaErrorInvalidValue;
-  switch (bmode) {
-    case B2: batched_fwd_kernel<B2><<<grid, THREADS, 0, stream>>>(a, k); break;
-    case B0: batched_fwd_kernel<B0><<<grid, THREADS, 0, stream>>>(a, k); break;
-    default: batched_fwd_kernel<BGEN><<<grid, THREADS, 0, stream>>>(a, k); break;
+  if (bmode == B2 && a.in_dtype == a.out_dtype) {
+    switch (a.in_dtype) {
+      case DT_U8: return launch_persistent<B2, TypedIO<uint8_t, uint8_t>>(a, k, stream);
+      case DT_F16: return launch_persistent<B2, TypedIO<__half, __half>>(a, k, stream);
+      case DT_BF16:
+        return launch_persistent<B2, TypedIO<__nv_bfloat16, __nv_bfloat16>>(a, k, stream);
+      default: return launch_persistent<B2, TypedIO<float, float>>(a, k, stream);
+    }
   }
-  return cudaGetLastError();
+  if (bmode == B2) return launch_persistent<B2, DynIO>(a, k, stream);
+  if (bmode == B0) return launch_persistent<B0, DynIO>(a, k, stream);
+  return launch_persistent<BGEN, DynIO>(a, k, stream);
 }
 
 }  // namespace wdweno

@@ -145,6 +145,60 @@ __device__ __forceinline__ void store4_vec(void* base, int64_t idx, float v0, fl
   }
 }
 
+// Two consecutive elements at `idx` (idx aligned to 2 elements, unit
+// stride) written with one vector store.
+__device__ __forceinline__ void store2_vec(void* base, int64_t idx, float v0, float v1, int dt,
+                                           int clampf) {
+  switch (dt) {
+    case DT_U8: {
+      const uint16_t packed = (uint16_t)(encode_u8(v0) | (encode_u8(v1) << 8));
+      *reinterpret_cast<uint16_t*>(static_cast<uint8_t*>(base) + idx) = packed;
+      break;
+    }
+    case DT_F16:
+      *reinterpret_cast<__half2*>(static_cast<__half*>(base) + idx) =
+          __floats2half2_rn(clamp_opt(v0, clampf), clamp_opt(v1, clampf));
+      break;
+    case DT_BF16:
+      *reinterpret_cast<__nv_bfloat162*>(static_cast<__nv_bfloat16*>(base) + idx) =
+          __floats2bfloat162_rn(clamp_opt(v0, clampf), clamp_opt(v1, clampf));
+      break;
+    default:
+      *reinterpret_cast<float2*>(static_cast<float*>(base) + idx) =
+          make_float2(clamp_opt(v0, clampf), clamp_opt(v1, clampf));
+      break;
+  }
+}
+
+// Typed variants (storage type fixed at compile time).
+__device__ __forceinline__ float to_float(uint8_t v) { return (float)v * (1.0f / 255.0f); }
+__device__ __forceinline__ float to_float(__half v) { return __half2float(v); }
+__device__ __forceinline__ float to_float(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float to_float(float v) { return v; }
+
+template <class T> struct DTypeOf;
+template <> struct DTypeOf<uint8_t> { static constexpr int value = DT_U8; };
+template <> struct DTypeOf<__half> { static constexpr int value = DT_F16; };
+template <> struct DTypeOf<__nv_bfloat16> { static constexpr int value = DT_BF16; };
+template <> struct DTypeOf<float> { static constexpr int value = DT_F32; };
+
+template <class T>
+__device__ __forceinline__ void store_typed(void* base, int64_t idx, float v, int clampf) {
+  store_elem(base, idx, v, DTypeOf<T>::value, clampf);  // the switch folds away
+}
+
+template <class T>
+__device__ __forceinline__ void store2_typed(void* base, int64_t idx, float v0, float v1,
+                                             int clampf) {
+  store2_vec(base, idx, v0, v1, DTypeOf<T>::value, clampf);
+}
+
+template <class T>
+__device__ __forceinline__ void store4_typed(void* base, int64_t idx, float v0, float v1,
+                                             float v2, float v3, int clampf) {
+  store4_vec(base, idx, v0, v1, v2, v3, DTypeOf<T>::value, clampf);
+}
+
 // ---------------------------------------------------------------------------
 // Directional blend of one new point (Eqs. alpha, IzrazOmega2d,
 // 2dKombinacija and their phase-2 counterparts).

@@ -17,7 +17,7 @@ struct FwdArgs {
   int64_t out_sc, out_sh, out_sw;
   int64_t orows, ocols;          // output extent (2n or 2n-1, ...)
   int64_t rows_per_band;
-  int out_vec;                   // unit column stride and 4-element aligned rows
+  int out_vec;                   // unit column stride and 2-element aligned rows
 };
 
 int tile_width_fwd();
