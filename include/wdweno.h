@@ -107,14 +107,15 @@ int weno_zoom2x_fwd(const weno_image* in, weno_dtype in_t, const weno_image* out
  *   grad_in   : FP32, shaped like x; overwritten (not accumulated)
  *   workspace : device scratch of >= weno_zoom2x_bwd_workspace_bytes(x)
  *               bytes, 16-byte aligned; no initialisation needed; it holds
- *               the recomputed phase-1 values and per-point adjoints
+ *               the recomputed indicators and phase-1 values, the per-point
+ *               adjoints and the per-stencil node coefficients
  * Returns WENO_OK, WENO_EINVAL, WENO_EWORKSPACE or WENO_ECUDA. */
 int weno_zoom2x_bwd(const weno_image* x, const weno_image* grad_out,
                     const weno_image* grad_in, const weno_params* p, void* workspace,
                     size_t workspace_bytes, void* stream);
 
 /* Scratch bytes weno_zoom2x_bwd needs for an input shaped like `x`
- * (19 FP32 values per cell of the image extended by 6 cells per side, per
+ * (55 FP32 values per cell of the image extended by 6 cells per side, per
  * channel).  Returns 0 for a malformed descriptor. */
 size_t weno_zoom2x_bwd_workspace_bytes(const weno_image* x);
 
@@ -128,8 +129,9 @@ size_t weno_zoom2x_batched_workspace_bytes(int count);
  *                 the call can be captured into a CUDA graph and replayed)
  *   workspace   : device buffer of >= weno_zoom2x_batched_workspace_bytes
  *                 bytes; contents need no initialisation and are scratch
- *   rows_per_tile, tile_width : tile shape (0 = library default); the
- *                 autotuner chooses these per size class
+ *   rows_per_tile, tile_width : tile shape (0 = library default: 64-row
+ *                 bands, 247-column strips); the autotuner chooses the band
+ *                 height per size class
  * Shapes follow weno_zoom2x_fwd per image; descriptors are read on the
  * device, so a malformed descriptor is skipped (its output is left
  * untouched) rather than reported.
@@ -140,9 +142,12 @@ int weno_zoom2x_batched(int count, const weno_image* d_in, weno_dtype in_t,
                         int tile_width, void* stream);
 
 /* weno_zoom2x_fwd with an explicit tile shape, for the autotuner.
- *   rows_per_tile : coarse rows per CTA band, 1..4096 (0 = default 64)
- *   tile_width    : coarse output columns per CTA; 0 or 240 (the built
- *                   strip width, 128 threads owning two columns each)
+ *   rows_per_tile : coarse rows per CTA band, 1..4096 (0 = the default:
+ *                   the band count that best balances the last wave of CTAs
+ *                   on this GPU against the per-band pipeline fill)
+ *   tile_width    : coarse output columns per CTA; 0 or 247 (the built
+ *                   strip width: 256 threads, one column each, 9 of them
+ *                   covering the dependency halo)
  * Returns as weno_zoom2x_fwd, or WENO_EINVAL for an unsupported shape and
  * WENO_ERANGE when the band count exceeds 65535. */
 int weno_zoom2x_fwd_tiled(const weno_image* in, weno_dtype in_t, const weno_image* out,

@@ -106,9 +106,12 @@ def _out_like(x: torch.Tensor, params: Params, layout: str, dtype) -> torch.Tens
 
 
 def zoom2x_fwd(x: torch.Tensor, params: Optional[Params] = None, out_dtype=None,
-               layout: str = "chw", rows_per_tile: int = 0,
+               layout: str = "chw", rows_per_tile: Optional[int] = None,
                out: Optional[torch.Tensor] = None) -> torch.Tensor:
-    """Forward 2x zoom (``weno_zoom2x_fwd``); no autograd."""
+    """Forward 2x zoom (``weno_zoom2x_fwd``); no autograd.
+
+    ``rows_per_tile``: band height per CTA; None = the autotuner's cached
+    choice for this size class (see ``autotune``), 0 = the library default."""
     params = params or Params()
     _require_cuda(x, "x")
     if x.numel() == 0:
@@ -116,6 +119,9 @@ def zoom2x_fwd(x: torch.Tensor, params: Optional[Params] = None, out_dtype=None,
     if out is None:
         out = _out_like(x, params, layout, out_dtype or x.dtype)
     _require_cuda(out, "out")
+    if rows_per_tile is None:
+        from . import autotune
+        rows_per_tile = autotune.lookup(x, out.dtype, layout)
     rc = B.weno_zoom2x_fwd_tiled(image(x, layout), _DT[x.dtype], image(out, layout),
                                  _DT[out.dtype], params.c(), rows_per_tile, 0,
                                  _stream(x.device))
@@ -229,6 +235,9 @@ class BatchedPlan:
 
 
 def zoom2x_batched(images: Sequence[torch.Tensor], params: Optional[Params] = None,
-                   out_dtype=None, layout: str = "chw", rows_per_tile: int = 0):
+                   out_dtype=None, layout: str = "chw", rows_per_tile: Optional[int] = None):
     """Zooms images of independent sizes in one persistent launch."""
+    if rows_per_tile is None:
+        from . import autotune
+        rows_per_tile = autotune.lookup_batched(images, out_dtype, layout)
     return BatchedPlan(images, params, out_dtype, layout, rows_per_tile).run()

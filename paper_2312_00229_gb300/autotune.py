@@ -1,0 +1,134 @@
+"""Autotuner for the tile shape of the forward and batched zoom.
+
+The CUDA kernels take the band height (coarse rows per CTA) as a run-time
+parameter; the strip width (247 columns, one thread per coarse column) is
+fixed by the build.  This module times candidate band heights on the current
+GPU with CUDA events and caches the fastest per size class in a JSON file,
+keyed by device name, storage types, layout and size class (planes and the
+image sides rounded up to powers of two).
+
+``api.zoom2x_fwd(..., rows_per_tile=None)`` consults the cache; a miss uses the
+library's own default (the band count that balances the last wave of CTAs).
+"""
+from __future__ import annotations
+
+import json
+import os
+import threading
+from typing import Dict, Iterable, Optional, Sequence
+
+import torch
+
+CACHE_PATH = os.environ.get(
+    "WDWENO_AUTOTUNE_CACHE",
+    os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json"))
+CANDIDATES = (0, 16, 24, 32, 48, 64, 96, 128, 192)
+
+_lock = threading.Lock()
+_cache: Optional[Dict[str, int]] = None
+_dev_names: Dict[int, str] = {}
+
+
+def _device_name(device) -> str:
+    idx = device.index if device.index is not None else torch.cuda.current_device()
+    if idx not in _dev_names:
+        _dev_names[idx] = torch.cuda.get_device_name(idx)
+    return _dev_names[idx]
+
+
+def _pow2(v: int) -> int:
+    p = 1
+    while p < v:
+        p <<= 1
+    return p
+
+
+def size_class(x: torch.Tensor, out_dtype, layout: str) -> str:
+    from .api import _planes
+    h, w, c, _, _, _ = _planes(x, layout)
+    dev = _device_name(x.device)
+    return "|".join([dev, str(x.dtype), str(out_dtype), layout, str(_pow2(int(c))),
+                     str(_pow2(int(h))), str(_pow2(int(w)))])
+
+
+def _load() -> Dict[str, int]:
+    global _cache
+    with _lock:
+        if _cache is None:
+            try:
+                with open(CACHE_PATH) as fh:
+                    _cache = {k: int(v) for k, v in json.load(fh).items()}
+            except (OSError, ValueError):
+                _cache = {}
+        return _cache
+
+
+def _save() -> None:
+    with _lock:
+        os.makedirs(os.path.dirname(CACHE_PATH), exist_ok=True)
+        tmp = CACHE_PATH + f".tmp{os.getpid()}"
+        with open(tmp, "w") as fh:
+            json.dump(_cache, fh, indent=1, sort_keys=True)
+        os.replace(tmp, CACHE_PATH)
+
+
+def lookup(x: torch.Tensor, out_dtype, layout: str) -> int:
+    """Cached band height for this size class, or 0 (library default)."""
+    return _load().get(size_class(x, out_dtype, layout), 0)
+
+
+def _time(fn, reps: int) -> float:
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def tune_fwd(x: torch.Tensor, params=None, out_dtype=None, layout: str = "chw",
+             candidates: Iterable[int] = CANDIDATES, reps: int = 10) -> Dict[int, float]:
+    """Times each candidate band height on `x` and caches the fastest.
+    Returns {rows_per_tile: milliseconds}."""
+    from . import api
+    params = params or api.Params()
+    odt = out_dtype or x.dtype
+    out = api._out_like(x, params, layout, odt)
+    times = {}
+    for r in candidates:
+        times[int(r)] = _time(lambda: api.zoom2x_fwd(x, params, layout=layout, rows_per_tile=r,
+                                                     out=out), reps)
+    best = min(times, key=times.get)
+    _load()[size_class(x, odt, layout)] = best
+    _save()
+    return times
+
+
+def tune_batched(images: Sequence[torch.Tensor], params=None, out_dtype=None,
+                 layout: str = "chw", candidates: Iterable[int] = (16, 32, 64, 128),
+                 reps: int = 5) -> Dict[int, float]:
+    """Times the persistent batched launch for each band height and caches
+    the fastest under the batch's size class (dtype, layout, image count)."""
+    from . import api
+    times = {}
+    plans = {}
+    for r in candidates:
+        plans[r] = api.BatchedPlan(images, params, out_dtype, layout, rows_per_tile=r)
+        times[int(r)] = _time(plans[r].run, reps)
+    best = min(times, key=times.get)
+    key = "|".join(["batched", _device_name(images[0].device),
+                    str(images[0].dtype), str(out_dtype or images[0].dtype), layout,
+                    str(_pow2(len(images)))])
+    _load()[key] = best
+    _save()
+    return times
+
+
+def lookup_batched(images: Sequence[torch.Tensor], out_dtype, layout: str) -> int:
+    key = "|".join(["batched", _device_name(images[0].device),
+                    str(images[0].dtype), str(out_dtype or images[0].dtype), layout,
+                    str(_pow2(len(images)))])
+    return _load().get(key, 0)

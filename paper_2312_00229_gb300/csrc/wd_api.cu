@@ -16,6 +16,44 @@ using namespace wdweno;
 namespace {
 
 constexpr int64_t kDefaultRowsPerBand = 64;
+constexpr int kFwdCtasPerSm = 2;  // 256 threads x 128 registers
+
+int sm_count() {
+  static int cached[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+  if (!cached[dev]) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+      cached[dev] = v;
+  }
+  return cached[dev];
+}
+
+// Band height for a one-launch forward: choose the number of bands B that
+// minimises (waves of CTAs) x (rows per band + pipeline fill), i.e. balance
+// the tail of the last wave against the fixed per-band cost.
+int64_t default_rows_per_band(int64_t n, int64_t m, int64_t planes) {
+  const int sms = sm_count();
+  if (sms <= 0) return kDefaultRowsPerBand;
+  const int64_t slots = (int64_t)sms * kFwdCtasPerSm;
+  const int64_t strips = (m + tile_width_fwd() - 1) / tile_width_fwd();
+  const int64_t base = strips * planes;
+  const int64_t fill = 6;
+  int64_t best_rpb = n, best_cost = -1;
+  for (int64_t bands = 1; bands <= 4096; ++bands) {
+    const int64_t rpb = (n + bands - 1) / bands;
+    if (rpb < 16 && bands > 1) break;
+    if (bands > 1 && (n + rpb - 1) / rpb != bands) continue;  // same rpb as a smaller count
+    const int64_t waves = (base * bands + slots - 1) / slots;
+    const int64_t cost = waves * (rpb + fill);
+    if (best_cost < 0 || cost < best_cost) {
+      best_cost = cost;
+      best_rpb = rpb;
+    }
+  }
+  return best_rpb < 1 ? 1 : best_rpb;
+}
 
 int64_t dtype_size(int dt) {
   switch (dt) {
@@ -164,7 +202,9 @@ int weno_zoom2x_fwd_tiled(const weno_image* in, weno_dtype in_t, const weno_imag
   MethodConsts k;
   int bmode;
   if (!fold_consts(p, &k, &bmode)) return WENO_EINVAL;
-  const int64_t rpb = rows_per_tile > 0 ? rows_per_tile : kDefaultRowsPerBand;
+  const int64_t rpb = rows_per_tile > 0 ? rows_per_tile
+                                        : default_rows_per_band(in->height, in->width,
+                                                                in->channels);
   FwdArgs a = make_fwd_args(in, in_t, out, out_t, orows, ocols, rpb);
   if ((a.n + rpb - 1) / rpb > 65535) return WENO_ERANGE;
   cudaError_t e = launch_zoom2x_fwd(a, k, bmode, static_cast<cudaStream_t>(stream));
