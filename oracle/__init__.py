@@ -78,11 +78,17 @@ def lib():
             L.oracle_directional.argtypes = [ctypes.c_double] * 4 + [
                 ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
             L.oracle_directional.restype = None
-            if hasattr(L, "oracle_weno1d_resample"):
-                L.oracle_weno1d_resample.argtypes = [ctypes.c_void_p, ctypes.c_int64,
-                                                     ctypes.c_void_p, ctypes.c_int64,
-                                                     ctypes.c_void_p, ctypes.c_double,
-                                                     ctypes.c_double, ctypes.c_double]
+            L.oracle_weno1d_cell.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.c_double,
+                                             ctypes.c_double, ctypes.c_double, ctypes.c_double]
+            L.oracle_weno1d_cell.restype = ctypes.c_double
+            L.oracle_weno_spline.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                             ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                             ctypes.c_double]
+            L.oracle_weno_spline.restype = ctypes.c_double
+            L.oracle_tensor_resample.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                                 ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                                 ctypes.c_double, ctypes.c_double,
+                                                 ctypes.c_double]
             _lib = L
     return _lib
 
@@ -135,3 +141,47 @@ def encode_u8(U) -> np.ndarray:
     out = np.empty(U.shape, dtype=np.uint8)
     lib().oracle_encode_u8(U.ctypes.data, U.size, out.ctypes.data)
     return out
+
+
+def weno1d_cell(v4, t, beta=2.0, k_eps=1e-8, h=1.0) -> float:
+    """1-D WENO interpolant of Sec. 2 on the cell [x_i, x_{i+1}] (t in [0, 1])."""
+    arr = (ctypes.c_double * 4)(*[float(v) for v in v4])
+    return lib().oracle_weno1d_cell(arr, float(t), float(beta), float(k_eps), float(h))
+
+
+def weno_spline(V, x, beta=2.0, k_eps=1e-8, h=1.0) -> float:
+    """WENO spline w(V, x) of Sec. 3.3 on the grid 0..n-1 (clamped ends)."""
+    V = np.ascontiguousarray(np.asarray(V, dtype=np.float64))
+    return lib().oracle_weno_spline(V.ctypes.data, V.size, 1, float(x), float(beta),
+                                    float(k_eps), float(h))
+
+
+def tensor_resample(A, out_h, out_w, beta=2.0, k_eps=1e-8, h=1.0) -> np.ndarray:
+    """Eq. (tensor): resample [..., n, m] planes to out_h x out_w on the
+    endpoint-aligned grids."""
+    A = np.ascontiguousarray(np.asarray(A, dtype=np.float64))
+    lead = A.shape[:-2]
+    n, m = A.shape[-2:]
+    planes = A.reshape(-1, n, m)
+    U = np.empty((planes.shape[0], out_h, out_w), dtype=np.float64)
+    for p in range(planes.shape[0]):
+        src = np.ascontiguousarray(planes[p])
+        rc = lib().oracle_tensor_resample(src.ctypes.data, n, m, U[p].ctypes.data, out_h, out_w,
+                                          float(beta), float(k_eps), float(h))
+        if rc != 0:
+            raise RuntimeError(f"oracle_tensor_resample failed with code {rc}")
+    return U.reshape(lead + (out_h, out_w))
+
+
+def zoom_to(A, out_h, out_w, beta=2.0, k_eps=1e-8, h=1.0) -> np.ndarray:
+    """Arbitrary-resolution zoom of Sec. 3.3: k successive WD WENO doublings
+    on the (2n-1) grid (Eq. zoomfactor) up to the first size >= the target in
+    both directions, then tensor WENO resampling to out_h x out_w.  Each
+    level's coarse spacing is half the previous level's."""
+    A = np.asarray(A, dtype=np.float64)
+    cur, hc = A, float(h)
+    while ((cur.shape[-2] < out_h and cur.shape[-2] > 1)
+           or (cur.shape[-1] < out_w and cur.shape[-1] > 1)):
+        cur = zoom2x(cur, beta=beta, k_eps=k_eps, h=hc, out_mode=OUT_2N_MINUS_1)
+        hc = hc / 2.0
+    return tensor_resample(cur, out_h, out_w, beta=beta, k_eps=k_eps, h=hc)

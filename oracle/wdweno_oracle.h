@@ -55,6 +55,18 @@ int oracle_zoom2x_planes(const double* A, int64_t planes, int64_t n, int64_t m,
 void oracle_directional(double n0, double n1, double n2, double scale_over_step,
                         double* p, double* si);
 
+/* 1-D WENO interpolant of Sec. 2 on one cell: v4 = samples at x_{i-1..i+2},
+ * t = (x - x_i)/h in [0, 1]. */
+double oracle_weno1d_cell(const double v4[4], double t, double beta, double k_eps, double h);
+
+/* WENO spline w(V, x), x in [0, n-1], samples V[k * stride] (Sec. 3.3). */
+double oracle_weno_spline(const double* V, int64_t n, int64_t stride, double x, double beta,
+                          double k_eps, double h);
+
+/* Tensor WENO resampling of one n x m plane to n_out x m_out (Eq. tensor). */
+int oracle_tensor_resample(const double* A, int64_t n, int64_t m, double* U, int64_t n_out,
+                           int64_t m_out, double beta, double k_eps, double h);
+
 /* Saturate to [0, 1], scale by 255, round half to even. */
 void oracle_encode_u8(const double* U, int64_t count, unsigned char* out);
 
