@@ -25,6 +25,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import re
 import statistics
@@ -52,6 +53,8 @@ FP32_LANES_PER_SM = 128
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "zoom2x_fwd_1080p_u8.md")
 KERNEL_SOURCES = ["paper_2312_00229_gb300/csrc/wd_fwd_tile.cuh",
                   "paper_2312_00229_gb300/csrc/wd_common.cuh",
+                  "paper_2312_00229_gb300/csrc/wd_fwd_kernels.cuh",
+                  "paper_2312_00229_gb300/csrc/wd_fwd_typed.cu",
                   "paper_2312_00229_gb300/csrc/wd_fwd.cu"]
 
 
@@ -496,6 +499,50 @@ def extras(torch, np, api, scenes, dev, world, hbm_peak):
                         "us": round(t8 * 1e6, 1),
                         "workload": "512x512x3 uint8 pixel art -> 4096x4096x3 uint8, "
                                     "FP32 intermediates"}
+    del pa
+    torch.cuda.empty_cache()
+
+    # arbitrary scale (Sec. 3.3): 1920x1080x3 uint8 -> 5760x3240x3 uint8
+    hd = torch.from_numpy(scenes.planar(scenes.piecewise_smooth(1080, 1920,
+                                                                seed=scenes.seed_for(2)))).to(dev)
+    o3 = torch.empty(3, 3240, 5760, dtype=torch.uint8, device=dev)
+    t_rs, _ = time_graph(torch, [lambda: api.resample(hd, 3240, 5760, out=o3)], 50)
+    t_z3, _ = time_graph(torch, [lambda: api.zoom_to(hd, 3240, 5760)], 20)
+    opx = 3240 * 5760
+    out["arbitrary_scale"] = {
+        "resample_gpix_s": round(world * opx / t_rs / 1e9, 4), "resample_us": round(t_rs * 1e6, 1),
+        "zoom_to_gpix_s": round(world * opx / t_z3 / 1e9, 4), "zoom_to_us": round(t_z3 * 1e6, 1),
+        "workload": "1920x1080x3 uint8 -> 5760x3240x3 uint8; resample = tensor WENO alone, "
+                    "zoom_to = two 2x passes on the 2n-1 grid (FP32 between) + tensor WENO "
+                    "down to 3x"}
+    del hd, o3
+    torch.cuda.empty_cache()
+
+    # inverse problem: recover 256x256x3 from its 512x512 zoom, 200 Adam steps
+    lo = scenes.planar(scenes.piecewise_smooth(256, 256, seed=scenes.seed_for(5, 1)))
+    x_true = torch.from_numpy(lo).to(dev).float() / 255.0
+    with torch.no_grad():
+        T = api.zoom2x_fwd(x_true)
+    xv = torch.zeros_like(x_true, requires_grad=True)
+    opt = torch.optim.Adam([xv], lr=1e-2)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(200):
+        opt.zero_grad()
+        ((api.zoom2x(xv) - T) ** 2).sum().backward()
+        opt.step()
+    e1.record()
+    torch.cuda.synchronize()
+    with torch.no_grad():
+        mse_x = float(((xv - x_true) ** 2).mean())
+        mse_z = float(((api.zoom2x_fwd(xv.detach()) - T) ** 2).mean())
+    out["inverse_problem"] = {
+        "ms_total": round(e0.elapsed_time(e1), 2), "steps": 200,
+        "psnr_recovered_db": round(10 * math.log10(1 / mse_x), 2),
+        "psnr_zoom_db": round(10 * math.log10(1 / mse_z), 2),
+        "workload": "256x256x3 FP32 from its 512x512 WD WENO zoom, Adam lr 1e-2 from zero, "
+                    "loss = sum of squared zoom error"}
     return out
 
 

@@ -154,6 +154,39 @@ int weno_zoom2x_fwd_tiled(const weno_image* in, weno_dtype in_t, const weno_imag
                           weno_dtype out_t, const weno_params* p, int rows_per_tile,
                           int tile_width, void* stream);
 
+/* Number of bounded waits in the forward kernels (plain and batched) that
+ * gave up on the current device since the library was loaded or the count
+ * was last reset.  The forward kernels request input rows asynchronously and
+ * wait for each with a time limit of one second; a wait that runs out marks
+ * the outputs of that call as invalid and lets the kernel finish instead of
+ * hanging.  Expected to stay 0.  Synchronises the device.
+ *   count : receives the count (host pointer)
+ *   reset : nonzero resets the count to 0 after reading
+ * Returns WENO_OK, WENO_EINVAL (null count) or WENO_ECUDA. */
+int weno_wait_timeouts(unsigned int* count, int reset);
+
+/* Tensor-product WENO resampling to an arbitrary size (Sec. 3.3, Eq.
+ * tensor): each output sample is the 1-D WENO interpolant of Sec. 2 (Eqs.
+ * TezinskiPolinom1d, IzrazOmega, with the linear weights that recover the
+ * cubic, Eq. PolinomZaVelikiStencil) across the columns of four 1-D
+ * interpolants down the rows.  The output grids are endpoint-aligned:
+ * output row r samples input row r (n-1)/(n_out-1) (0 when n_out = 1), and
+ * likewise for columns; samples outside the image are clamped to the edge.
+ *   in  : n x m x C, type in_t;  out : any n_out x m_out x C, type out_t
+ *   p   : beta, k_eps and h (eps_h = k_eps h^2, h = the input grid spacing;
+ *         eps_h is floored at 1e-30); si_scale and out_mode are ignored;
+ *         clamp_float as for the zoom
+ * Output sizes down to half the input's per axis use a separable tiled
+ * kernel; larger reductions fall back to one thread per output sample.
+ * Values are expected below ~1e18 in magnitude (squared differences must
+ * stay finite in FP32).
+ * The second stage of the arbitrary-scale zoom: k doublings on the
+ * (2n-1) grid (Eq. zoomfactor) followed by this resampling.
+ * Returns WENO_OK, WENO_EINVAL, WENO_EDTYPE, WENO_ERANGE (more than 524280
+ * output rows) or WENO_ECUDA. */
+int weno_resample(const weno_image* in, weno_dtype in_t, const weno_image* out,
+                  weno_dtype out_t, const weno_params* p, void* stream);
+
 /* weno_zoom2x_batched without a workspace, for callers that cannot allocate
  * device memory (for example code inside another application's real-time
  * video pipeline, where cudaMalloc may synchronise the device and stall every

@@ -179,14 +179,72 @@ def cascade_zoom(x: torch.Tensor, levels: int, params: Optional[Params] = None, 
                  inter_dtype=torch.float32, layout: str = "chw") -> torch.Tensor:
     """``levels`` successive 2x zooms (Sec. 3.3, Eq. zoomfactor); the
     intermediate images are kept in ``inter_dtype`` and only the last one is
-    encoded to ``out_dtype``."""
+    encoded to ``out_dtype``.  Each level's coarse grid is the previous
+    level's fine grid, so its spacing ``h`` is half the previous one."""
     params = params or Params()
     cur = x
     for lvl in range(levels):
         last = lvl == levels - 1
-        cur = zoom2x_fwd(cur, params, out_dtype=(out_dtype or x.dtype) if last else inter_dtype,
+        p = dataclasses.replace(params, h=params.h / (1 << lvl))
+        cur = zoom2x_fwd(cur, p, out_dtype=(out_dtype or x.dtype) if last else inter_dtype,
                          layout=layout)
     return cur
+
+
+def _hw(t: torch.Tensor, layout: str):
+    h, w, _, _, _, _ = _planes(t, layout)
+    return int(h), int(w)
+
+
+def resample(x: torch.Tensor, out_h: int, out_w: int, params: Optional[Params] = None,
+             out_dtype=None, layout: str = "chw", out: Optional[torch.Tensor] = None):
+    """Tensor-product WENO resampling (Sec. 3.3, Eq. tensor) to any
+    ``out_h x out_w`` on endpoint-aligned grids (``weno_resample``).
+    ``params.h`` is the spacing of the input grid; ``out_mode`` and
+    ``si_scale`` do not apply."""
+    params = params or Params()
+    _require_cuda(x, "x")
+    if x.numel() == 0 or out_h < 1 or out_w < 1:
+        raise ValueError("empty input or output")
+    if out is None:
+        shape = list(x.shape)
+        if layout == "hwc":
+            shape[0], shape[1] = out_h, out_w
+        else:
+            shape[-2], shape[-1] = out_h, out_w
+        out = torch.empty(shape, dtype=out_dtype or x.dtype, device=x.device)
+    _require_cuda(out, "out")
+    rc = B.weno_resample(image(x, layout), _DT[x.dtype], image(out, layout), _DT[out.dtype],
+                         params.c(), _stream(x.device))
+    B.check("weno_resample", rc)
+    return out
+
+
+def zoom_levels(n: int, m: int, out_h: int, out_w: int) -> int:
+    """Doublings on the (2n-1) grid (Eq. zoomfactor: n -> 2^k (n-1) + 1)
+    until both sides reach the target (sides of one sample never grow)."""
+    k = 0
+    while (n > 1 and n < out_h) or (m > 1 and m < out_w):
+        n, m, k = 2 * n - 1, 2 * m - 1, k + 1
+    return k
+
+
+def zoom_to(x: torch.Tensor, out_h: int, out_w: int, params: Optional[Params] = None,
+            out_dtype=None, inter_dtype=torch.float32, layout: str = "chw") -> torch.Tensor:
+    """Arbitrary-resolution zoom (Sec. 3.3): k WD WENO doublings on the
+    (2n-1) grid up to the first size that covers the target, then tensor
+    WENO resampling down to ``out_h x out_w`` (the 3x example zooms n to
+    4n-3, then resamples to 3n)."""
+    params = params or Params()
+    n, m = _hw(x, layout)
+    k = zoom_levels(n, m, out_h, out_w)
+    cur = x
+    p = dataclasses.replace(params, out_mode=B.WENO_OUT_2N_MINUS_1)
+    for lvl in range(k):
+        cur = zoom2x_fwd(cur, dataclasses.replace(p, h=params.h / (1 << lvl)),
+                         out_dtype=inter_dtype, layout=layout)
+    return resample(cur, out_h, out_w, dataclasses.replace(params, h=params.h / (1 << k)),
+                    out_dtype=out_dtype or x.dtype, layout=layout)
 
 
 class BatchedPlan:

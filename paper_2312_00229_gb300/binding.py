@@ -28,6 +28,8 @@ EXPORTS = (
     "weno_zoom2x_batched_workspace_bytes",
     "weno_zoom2x_batched",
     "weno_zoom2x_batched_noalloc",
+    "weno_resample",
+    "weno_wait_timeouts",
 )
 WENO_NOALLOC_MAX_IMAGES = 4096
 
@@ -73,6 +75,8 @@ _SIGS = {
                              ctypes.c_size_t, ctypes.c_int, ctypes.c_int, _VP], ctypes.c_int),
     "weno_zoom2x_batched_noalloc": ([ctypes.c_int, _VP, ctypes.c_int, _VP, ctypes.c_int, _PRM,
                                      ctypes.c_int, ctypes.c_int, _VP], ctypes.c_int),
+    "weno_resample": ([_IMG, ctypes.c_int, _IMG, ctypes.c_int, _PRM, _VP], ctypes.c_int),
+    "weno_wait_timeouts": ([ctypes.POINTER(ctypes.c_uint), ctypes.c_int], ctypes.c_int),
 }
 
 _lock = threading.Lock()
@@ -160,3 +164,15 @@ def weno_zoom2x_batched_noalloc(count, d_in, in_t, d_out, out_t, params, rows_pe
     return load().weno_zoom2x_batched_noalloc(int(count), d_in, in_t, d_out, out_t,
                                               ctypes.byref(params) if params is not None else None,
                                               int(rows_per_tile), int(tile_width), stream)
+
+
+def weno_resample(inp, in_t, out, out_t, params, stream) -> int:
+    return load().weno_resample(ctypes.byref(inp), in_t, ctypes.byref(out), out_t,
+                                ctypes.byref(params) if params is not None else None, stream)
+
+
+def weno_wait_timeouts(reset: bool = False) -> int:
+    """Abandoned bounded waits of the forward kernels (raises on error)."""
+    v = ctypes.c_uint(0)
+    check("weno_wait_timeouts", load().weno_wait_timeouts(ctypes.byref(v), 1 if reset else 0))
+    return int(v.value)

@@ -1,6 +1,7 @@
 // C ABI of the WD WENO library (declarations and contracts: include/wdweno.h).
 // Host-side argument validation, folding of the method's constants, and
 // kernel dispatch.  Nothing here allocates memory.
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -9,6 +10,7 @@
 #include "wd_batched.h"
 #include "wd_common.cuh"
 #include "wd_fwd.h"
+#include "wd_resample.h"
 #include "wdweno.h"
 
 using namespace wdweno;
@@ -160,6 +162,8 @@ FwdArgs make_fwd_args(const weno_image* in, int in_t, const weno_image* out, int
   const uintptr_t base = reinterpret_cast<uintptr_t>(out->data);
   a.out_vec = (out->stride_w == 1) && (out->stride_h % 2 == 0) && (out->stride_c % 2 == 0) &&
               (base % uintptr_t(2 * esz) == 0);
+  a.in_bulk = input_bulk_ok(in->data, dtype_size(in_t), in->width, in->channels,
+                            in->stride_c, in->stride_h, in->stride_w);
   return a;
 }
 
@@ -288,6 +292,38 @@ int weno_zoom2x_batched(int count, const weno_image* d_in, weno_dtype in_t,
   a.rows_per_band = rows_per_tile > 0 ? rows_per_tile : kDefaultRowsPerBand;
   a.workspace = workspace;
   cudaError_t e = launch_zoom2x_batched(a, k, bmode, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? WENO_OK : WENO_ECUDA;
+}
+
+int weno_wait_timeouts(unsigned int* count, int reset) {
+  if (!count) return WENO_EINVAL;
+  return fwd_wait_timeouts(count, reset != 0) == cudaSuccess ? WENO_OK : WENO_ECUDA;
+}
+
+int weno_resample(const weno_image* in, weno_dtype in_t, const weno_image* out,
+                  weno_dtype out_t, const weno_params* pp, void* stream) {
+  const weno_params p = pp ? *pp : weno_params_default();
+  if (!image_ok(in) || !image_ok(out)) return WENO_EINVAL;
+  if (dtype_size(in_t) == 0 || dtype_size(out_t) == 0) return WENO_EDTYPE;
+  if (out->channels != in->channels) return WENO_EINVAL;
+  if (overlaps(in, dtype_size(in_t), out, dtype_size(out_t))) return WENO_EINVAL;
+  if ((out->height + 7) / 8 > 65535) return WENO_ERANGE;
+  MethodConsts k;
+  int bmode;
+  if (!fold_consts(p, &k, &bmode)) return WENO_EINVAL;
+  ResampleArgs a;
+  a.in = in->data;
+  a.out = out->data;
+  a.in_dtype = in_t;
+  a.out_dtype = out_t;
+  a.n = in->height; a.m = in->width; a.planes = in->channels;
+  a.n_out = out->height; a.m_out = out->width;
+  a.in_sc = in->stride_c; a.in_sh = in->stride_h; a.in_sw = in->stride_w;
+  a.out_sc = out->stride_c; a.out_sh = out->stride_h; a.out_sw = out->stride_w;
+  a.clamp_float = p.clamp_float ? 1 : 0;
+  // a floor of 1e-30 keeps the larger indicator a normal FP32 number
+  const float eps = std::max(float(double(p.k_eps) * double(p.h) * double(p.h)), 1e-30f);
+  cudaError_t e = launch_resample(a, eps, p.beta, bmode, static_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? WENO_OK : WENO_ECUDA;
 }
 

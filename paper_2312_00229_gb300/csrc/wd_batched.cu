@@ -131,7 +131,10 @@ __global__ void __launch_bounds__(THREADS, WDWENO_FWD_MIN_BLOCKS)
     const unsigned long long per_plane = strips * bands;
     const int64_t plane = (int64_t)(local / per_plane);
     const unsigned long long rem = local % per_plane;
-    fwd_tile::zoom2x_fwd_tile<BMODE, IO>(f, k, ex, (int64_t)(rem % strips),
+    // register input path: the queue mixes images whose rows may not allow
+    // bulk copies, and one kernel holding both paths spills
+    f.in_bulk = 0;
+    fwd_tile::zoom2x_fwd_tile<BMODE, IO, false>(f, k, ex, (int64_t)(rem % strips),
                                          (int64_t)(rem / strips), plane);
   }
 }
@@ -179,6 +182,10 @@ cudaError_t launch_zoom2x_batched(const BatchedArgs& a, const MethodConsts& k, i
   if (bmode == B2) return launch_persistent<B2, DynIO>(a, k, stream);
   if (bmode == B0) return launch_persistent<B0, DynIO>(a, k, stream);
   return launch_persistent<BGEN, DynIO>(a, k, stream);
+}
+
+cudaError_t fwd_wait_timeouts_batched(unsigned int* count, bool reset) {
+  return fwd_tile::read_wait_timeouts(count, reset);
 }
 
 }  // namespace wdweno

@@ -25,4 +25,13 @@ cudaError_t launch_zoom2x_fwd(const FwdArgs& a, const MethodConsts& k, int bmode
   return fwd_kernels::launch_fwd<BGEN, DynIO>(a, k, stream);
 }
 
+cudaError_t fwd_wait_timeouts(unsigned int* count, bool reset) {
+  unsigned int a = 0, b = 0, c = 0;
+  cudaError_t e = fwd_tile::read_wait_timeouts(&a, reset);
+  if (e == cudaSuccess) e = fwd_wait_timeouts_typed(&b, reset);
+  if (e == cudaSuccess) e = fwd_wait_timeouts_batched(&c, reset);
+  *count = a + b + c;
+  return e;
+}
+
 }  // namespace wdweno

@@ -18,11 +18,26 @@ struct FwdArgs {
   int64_t orows, ocols;          // output extent (2n or 2n-1, ...)
   int64_t rows_per_band;
   int out_vec;                   // unit column stride and 2-element aligned rows
+  int in_bulk;                   // input rows by bulk copy (input_bulk_ok)
 };
+
+// Whether the forward kernel takes input rows by bulk copy: unit column
+// stride, 16-byte aligned base, row and plane strides and row length, and
+// 1- or 2-byte storage (FP32 rows measured faster through register loads).
+__host__ __device__ inline int input_bulk_ok(const void* base, int64_t esz, int64_t m,
+                                             int64_t planes, int64_t sc, int64_t sh, int64_t sw) {
+  return esz <= 2 && sw == 1 && (reinterpret_cast<uintptr_t>(base) % 16) == 0 &&
+         (sh * esz) % 16 == 0 && (planes == 1 || (sc * esz) % 16 == 0) && (m * esz) % 16 == 0;
+}
 
 int tile_width_fwd();
 int threads_fwd();
 cudaError_t launch_zoom2x_fwd(const FwdArgs& a, const MethodConsts& k, int bmode,
                               cudaStream_t stream);
+// Abandoned bounded waits counted by the forward kernels of each translation
+// unit (summed; optionally reset).
+cudaError_t fwd_wait_timeouts(unsigned int* count, bool reset);
+cudaError_t fwd_wait_timeouts_typed(unsigned int* count, bool reset);
+cudaError_t fwd_wait_timeouts_batched(unsigned int* count, bool reset);
 
 }  // namespace wdweno

@@ -31,7 +31,19 @@
 //   store             fine row 2(s-5): [A, E], fine row 2(s-6)+1: [S, X]
 // Barrier B1 opens the step; barrier B2 separates the exchange of the
 // phase-2 indicator sums inside the step.
+//
+// Input path.  When the input rows are 16-byte aligned (FwdArgs::in_bulk),
+// thread 0 requests each input row segment of the strip (with its halo)
+// KAHEAD steps ahead as one asynchronous bulk copy into a ring of RING raw
+// rows in shared memory, completing on the slot's mbarrier.  In step s,
+// after barrier B2, every thread waits for row s and decodes its own
+// (clamped) column of it into the float ring (first read in step s+1).  The sweep's barriers do not wait for these copies, unlike
+// register loads issued before them, so the DRAM latency is covered by
+// KAHEAD steps of work.  Other layouts (INB = false) load each row into a
+// register two steps ahead.
 #pragma once
+
+#include <cstddef>
 
 #include "wd_common.cuh"
 #include "wd_fwd.h"
@@ -43,6 +55,14 @@ constexpr int THREADS = 256;
 constexpr int HALO_L = 4;            // columns before the strip
 constexpr int TILE_W = THREADS - 9;  // output columns per CTA
 constexpr int ROW = THREADS + 4;     // floats per staged row (2 pad each side)
+constexpr int RING = 8;              // raw input rows in flight or in use
+constexpr int KAHEAD = 6;            // rows requested ahead of the sweep (< RING)
+// Raw bytes of one strip row: 256 FP32 columns plus up to 16 bytes of
+// alignment slack at each end.
+constexpr int RAW_BYTES = THREADS * 4 + 32;
+// Bound on one wait for an input row (nanoseconds of global time).
+constexpr unsigned long long WAIT_LIMIT_NS = 1000000000ull;
+static_assert(KAHEAD < RING && (RING & (RING - 1)) == 0, "input ring shape");
 
 struct __align__(16) Exchange {
   float A[8][ROW];            // input rows, slot = row & 7, column c at t + 2
@@ -51,7 +71,40 @@ struct __align__(16) Exchange {
                               // column c at t + 1
   float4 VS[THREADS + 2];     // S-point SIs summed over rows r-1, r (column c at t + 1)
   float4 VE[THREADS + 2];     // E-point SIs summed over rows r-1, r
+  // --- everything above is zeroed at the start of a tile ---
+  unsigned char raw[RING][RAW_BYTES];  // bulk-copied input rows, slot = load index % RING
+  uint64_t mbar[RING];                 // completion barrier of each slot
 };
+static_assert(offsetof(Exchange, raw) % 16 == 0 && RAW_BYTES % 16 == 0, "bulk destinations");
+
+// Bounded waits that gave up in the kernels of this translation unit (each
+// kernel TU has its own counter; see read_wait_timeouts).
+static __device__ unsigned int g_wait_timeouts;
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Waits for an input row; false after WAIT_LIMIT_NS.
+__device__ __forceinline__ bool wait_row(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  while (!mbar_try_wait(bar, parity))
+    if (global_ns() - t0 > WAIT_LIMIT_NS) return false;
+  return true;
+}
+
+// Host side: this TU's count of abandoned waits (optionally reset to 0).
+static inline cudaError_t read_wait_timeouts(unsigned int* v, bool reset) {
+  cudaError_t e = cudaMemcpyFromSymbol(v, g_wait_timeouts, sizeof(unsigned int));
+  if (e == cudaSuccess && reset) {
+    const unsigned int z = 0;
+    e = cudaMemcpyToSymbol(g_wait_timeouts, &z, sizeof(unsigned int));
+  }
+  return e;
+}
 
 __device__ __forceinline__ int64_t clamp64(int64_t v, int64_t lo, int64_t hi) {
   return v < lo ? lo : (v > hi ? hi : v);
@@ -70,7 +123,7 @@ struct Carry {
   float SIE[2][4], SIS[2][4], pS[2][6];          // stage 4
 };
 
-template <int BMODE, class IO>
+template <int BMODE, class IO, bool INB>
 struct FwdTile {
   // Arguments are held by value so that they stay in registers across the
   // barriers (a reference would be re-read from memory after each one).
@@ -86,6 +139,8 @@ struct FwdTile {
   int64_t out_base, out_sh;  // element index of (fine row 0, fine column 2c)
   int64_t out_sw;
   bool col_ok, vec_ok, odd_ok;
+  int own_off;               // INB: byte offset of this thread's clamped column in a raw row
+  int raw_len;               // INB: bytes copied per raw row
 
   __device__ __forceinline__ FwdTile(const FwdArgs& a, const MethodConsts& k_, Exchange& ex_,
                                      int64_t bx, int64_t by, int64_t plane)
@@ -108,6 +163,37 @@ struct FwdTile {
     out_sw = a.out_sw;
     out_sh = a.out_sh;
     out_base = plane * a.out_sc + 2 * c * a.out_sw;
+    if (INB) {
+      // window = the strip's columns b0-4 .. b0+251 inside the image, widened
+      // to 16-byte boundaries (the row length is a multiple of 16 bytes)
+      const int64_t esz = IO::in_size(in_dtype);
+      const int64_t lo = ((b0 - HALO_L > 0 ? b0 - HALO_L : 0) * esz) & ~int64_t(15);
+      int64_t hi_c = b0 - HALO_L + THREADS;
+      if (hi_c > a.m) hi_c = a.m;
+      const int64_t hi = (hi_c * esz + 15) & ~int64_t(15);
+      raw_len = (int)(hi - lo);
+      own_off = (int)(clamp64(c, 0, a.m - 1) * esz - lo);
+    } else {
+      raw_len = 0;
+      own_off = 0;
+    }
+  }
+
+  // Thread 0: requests input row r (clamped) as load number j into its slot.
+  __device__ __forceinline__ void issue_row(int j, int r) const {
+    const int rc = r < 0 ? 0 : (r > n - 1 ? n - 1 : r);
+    // thread 0's in_idx is the first window column of row 0; own_off its offset
+    const unsigned char* src = static_cast<const unsigned char*>(in) +
+                               (in_idx + (int64_t)rc * in_sh) * IO::in_size(in_dtype) - own_off;
+    uint64_t* bar = &ex.mbar[j & (RING - 1)];
+    mbar_arrive_expect_tx(bar, (uint32_t)raw_len);
+    bulk_g2s(ex.raw[j & (RING - 1)], src, (uint32_t)raw_len, bar);
+  }
+
+  // Waits (bounded) for load number j.
+  __device__ __forceinline__ void await_row(int j) const {
+    if (!wait_row(&ex.mbar[j & (RING - 1)], (uint32_t)(j / RING) & 1u))
+      atomicAdd(&g_wait_timeouts, 1u);
   }
 
   __device__ __forceinline__ float load_row(int r) const {
@@ -140,12 +226,21 @@ struct FwdTile {
     if (rs > H + 5) return;  // padding step past the band (uniform)
     const float w = k.w;
 
-    const float cur = pf;    // input row s, loaded in step s-2
-    pf = pf2;
-    pf2 = load_row(s + 2);   // prefetch two rows ahead
+    const int j = rs + HALO_L;  // load number of row s (the sweep starts at a0 - 4)
+    float cur = 0.f;
+    if (!INB) {
+      cur = pf;               // input row s, loaded in step s-2
+      pf = pf2;
+      pf2 = load_row(s + 2);  // prefetch two rows ahead
+    }
 
     __syncthreads();  // B1: rows published in step s-1 are visible
-    ex.A[s & 7][t + 2] = cur;
+    if (INB) {
+      // the slot of load j + KAHEAD was last decoded in step s-2
+      if (t == 0 && rs + KAHEAD <= H + 5) issue_row(j + KAHEAD, s + KAHEAD);
+    } else {
+      ex.A[s & 7][t + 2] = cur;
+    }
 
     // Input rows s-3, s-2, s-1 at columns c-1..c+2 (index u + 1).
     float a1[4], a2[4], a3[4];
@@ -277,6 +372,12 @@ struct FwdTile {
     }
 
     __syncthreads();  // B2
+    if (INB) {
+      // input row s (slot s & 7 last held row s-8, last read in step s-3);
+      // first read in step s+1, so this wait delays no barrier
+      await_row(j);
+      ex.A[s & 7][t + 2] = IO::decode(ex.raw[j & (RING - 1)] + own_off, in_dtype);
+    }
 
     // ---- stage 5: E(s-5, c) and S(s-6, c) -----------------------------------
     if (rs >= 5 && rs <= H + 4) {
@@ -310,7 +411,15 @@ struct FwdTile {
     __syncthreads();
     {
       float* z = reinterpret_cast<float*>(&ex);
-      for (int i = t; i < (int)(sizeof(Exchange) / sizeof(float)); i += THREADS) z[i] = 0.f;
+      for (int i = t; i < (int)(offsetof(Exchange, raw) / sizeof(float)); i += THREADS) z[i] = 0.f;
+    }
+    const int s_begin = a0 - 4;
+    const int s_end = a0 + H + 5;  // inclusive
+    const int loads = s_end - s_begin + 1;
+    if (INB && t == 0) {
+      for (int i = 0; i < RING; ++i) mbar_init(&ex.mbar[i], 1);
+      fence_mbar_init();
+      for (int j = 0; j < KAHEAD && j < loads; ++j) issue_row(j, s_begin + j);
     }
     Carry C;
 #pragma unroll
@@ -323,13 +432,25 @@ struct FwdTile {
       for (int d = 0; d < 6; ++d) C.px[i][d] = C.pS[i][d] = 0.f;
       C.sXc[i] = C.qXc[i] = C.sVc[i] = C.qVc[i] = 0.f;
     }
-    const int s_begin = a0 - 4;
-    const int s_end = a0 + H + 5;  // inclusive
-    float pf = load_row(s_begin);
-    float pf2 = load_row(s_begin + 1);
+    float pf = INB ? 0.f : load_row(s_begin);
+    float pf2 = INB ? 0.f : load_row(s_begin + 1);
     for (int s = s_begin; s <= s_end; s += 2) {
       step<0>(s, pf, pf2, C);
       step<1>(s + 1, pf, pf2, C);
+    }
+    if (INB) {
+      __syncthreads();  // every thread has decoded its last row
+      if (t == 0) {
+        // Every issued row was waited for; after an abandoned wait a copy
+        // may still be in flight, so wait (bounded) for each slot's last
+        // load before the barriers are invalidated and the memory reused.
+        for (int i = 0; i < RING && i < loads; ++i) {
+          const int last = i + ((loads - 1 - i) / RING) * RING;
+          if (!wait_row(&ex.mbar[i], (uint32_t)(last / RING) & 1u)) atomicAdd(&g_wait_timeouts, 1u);
+          mbar_inval(&ex.mbar[i]);
+        }
+      }
+      __syncthreads();
     }
   }
 };
@@ -339,6 +460,10 @@ template <class TIn, class TOut>
 struct TypedIO {
   __device__ __forceinline__ static float load(const void* base, int64_t idx, int) {
     return to_float(__ldg(static_cast<const TIn*>(base) + idx));
+  }
+  __device__ __forceinline__ static int in_size(int) { return (int)sizeof(TIn); }
+  __device__ __forceinline__ static float decode(const unsigned char* p, int) {
+    return to_float(*reinterpret_cast<const TIn*>(p));
   }
   __device__ __forceinline__ static void store1(void* out, int64_t idx, float v, int, int clampf) {
     store_typed<TOut>(out, idx, v, clampf);
@@ -354,6 +479,17 @@ struct DynIO {
   __device__ __forceinline__ static float load(const void* base, int64_t idx, int dt) {
     return load_elem(base, idx, dt);
   }
+  __device__ __forceinline__ static int in_size(int dt) {
+    return dt == DT_U8 ? 1 : (dt == DT_F32 ? 4 : 2);
+  }
+  __device__ __forceinline__ static float decode(const unsigned char* p, int dt) {
+    switch (dt) {
+      case DT_U8: return to_float(*p);
+      case DT_F16: return to_float(*reinterpret_cast<const __half*>(p));
+      case DT_BF16: return to_float(*reinterpret_cast<const __nv_bfloat16*>(p));
+      default: return *reinterpret_cast<const float*>(p);
+    }
+  }
   __device__ __forceinline__ static void store1(void* out, int64_t idx, float v, int dt,
                                                 int clampf) {
     store_elem(out, idx, v, dt, clampf);
@@ -364,11 +500,11 @@ struct DynIO {
   }
 };
 
-template <int BMODE, class IO>
+template <int BMODE, class IO, bool INB>
 __device__ __forceinline__ void zoom2x_fwd_tile(const FwdArgs& a, const MethodConsts& k,
                                                 Exchange& ex, int64_t bx, int64_t by,
                                                 int64_t plane) {
-  FwdTile<BMODE, IO> tile(a, k, ex, bx, by, plane);
+  FwdTile<BMODE, IO, INB> tile(a, k, ex, bx, by, plane);
   tile.run();
 }
 

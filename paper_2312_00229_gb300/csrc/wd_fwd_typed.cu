@@ -21,4 +21,8 @@ cudaError_t launch_fwd_typed(const FwdArgs& a, const MethodConsts& k, cudaStream
   return cudaSuccess;
 }
 
+cudaError_t fwd_wait_timeouts_typed(unsigned int* count, bool reset) {
+  return fwd_tile::read_wait_timeouts(count, reset);
+}
+
 }  // namespace wdweno

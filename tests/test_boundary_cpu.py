@@ -148,3 +148,33 @@ def test_descriptor_folding_on_host_tensors():
 def test_api_refuses_cpu_tensors():
     with pytest.raises(ValueError):
         api.zoom2x_fwd(torch.zeros(1, 4, 4))
+
+
+def test_resample_rejects_bad_arguments_without_launching():
+    p = B.weno_params_default()
+    good_in = _img(FAKE_IN, 4, 5, 3)
+    good_out = _img(FAKE_OUT, 11, 2, 3)
+    cases = [
+        (_img(0, 4, 5, 3), good_out, B.WENO_U8, B.WENO_U8, B.WENO_EINVAL),        # null
+        (good_in, _img(FAKE_OUT, 0, 2, 3), B.WENO_U8, B.WENO_U8, B.WENO_EINVAL),  # empty out
+        (good_in, _img(FAKE_OUT, 11, 2, 2), B.WENO_U8, B.WENO_U8, B.WENO_EINVAL),  # channels
+        (good_in, good_out, 9, B.WENO_U8, B.WENO_EDTYPE),
+        (good_in, _img(FAKE_IN + 3, 11, 2, 3), B.WENO_U8, B.WENO_U8, B.WENO_EINVAL),  # overlap
+        (_img(FAKE_IN, 4, 5, 70000), _img(FAKE_OUT, 6, 6, 70000), B.WENO_U8, B.WENO_U8,
+         B.WENO_EINVAL),  # channels < 65536
+        (good_in, _img(FAKE_OUT, 600000, 2, 3), B.WENO_U8, B.WENO_U8, B.WENO_ERANGE),
+    ]
+    for i, (a, b, ta, tb, want) in enumerate(cases):
+        assert B.weno_resample(a, ta, b, tb, p, None) == want, i
+    bad = B.weno_params_default()
+    bad.beta = float("nan")
+    assert B.weno_resample(good_in, 0, good_out, 0, bad, None) == B.WENO_EINVAL
+
+
+def test_api_zoom_levels_and_cpu_refusal():
+    assert api.zoom_levels(1080, 1920, 3240, 5760) == 2
+    assert api.zoom_levels(5, 5, 4, 4) == 0
+    with pytest.raises(ValueError):
+        api.resample(torch.zeros(1, 4, 4), 8, 8)
+    with pytest.raises(ValueError):
+        api.zoom_to(torch.zeros(1, 4, 4), 8, 8)

@@ -56,7 +56,7 @@ def test_bwd_random(shape, mode):
     _check(A, G, params)
 
 
-@pytest.mark.parametrize("beta", [0.0, 1.0, 3.0])
+@pytest.mark.parametrize("beta", [0.0, 0.1, 1.0, 3.0])
 def test_bwd_beta(beta):
     params = api.Params(beta=beta)
     A = RNG.random((1, 12, 17))
