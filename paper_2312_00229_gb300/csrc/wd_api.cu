@@ -321,6 +321,9 @@ int weno_resample(const weno_image* in, weno_dtype in_t, const weno_image* out,
   a.in_sc = in->stride_c; a.in_sh = in->stride_h; a.in_sw = in->stride_w;
   a.out_sc = out->stride_c; a.out_sh = out->stride_h; a.out_sw = out->stride_w;
   a.clamp_float = p.clamp_float ? 1 : 0;
+  a.out_vec4 = out->stride_w == 1 && out->stride_h % 4 == 0 && out->stride_c % 4 == 0 &&
+               reinterpret_cast<uintptr_t>(out->data) % uintptr_t(4 * dtype_size(out_t)) == 0;
+  a.win_rows = 0;
   // a floor of 1e-30 keeps the larger indicator a normal FP32 number
   const float eps = std::max(float(double(p.k_eps) * double(p.h) * double(p.h)), 1e-30f);
   cudaError_t e = launch_resample(a, eps, p.beta, bmode, static_cast<cudaStream_t>(stream));

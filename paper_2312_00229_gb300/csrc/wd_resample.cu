@@ -14,6 +14,8 @@
 // One thread per output pixel: four 1-D interpolants down the columns of
 // the 4x4 input window (z_k = w(A(:,k), y)), then one across them
 // (U = w(Z, x)).  Inputs outside the image are clamped to the edge.
+#include <type_traits>
+
 #include "wd_common.cuh"
 #include "wd_resample.h"
 
@@ -93,35 +95,77 @@ __global__ void __launch_bounds__(256) resample_kernel(ResampleArgs a, float eps
              a.clamp_float);
 }
 
-// Separable tiled form for scales down to 1/2 in x: a CTA owns RS_TR
-// output rows x RS_TC output columns of one plane.  Pass 1 forms the column
-// interpolants z(r, k) = w(A(:, k), y_r) for the tile's rows and every input
-// column its outputs read (at most 2 RS_TC + 5 of them), into shared memory;
-// pass 2 interpolates each output across four of them.  Per output this is
-// about 1 + (in/out column ratio) + small halo 1-D interpolants instead of 5.
+// Storage access: a concrete element type, or Dyn for the run-time type.
+struct Dyn {};
+
+template <class T>
+__device__ __forceinline__ float rs_load(const void* base, int64_t idx, int dt) {
+  if constexpr (std::is_same<T, Dyn>::value) {
+    return load_elem(base, idx, dt);
+  } else {
+    return to_float(__ldg(static_cast<const T*>(base) + idx));
+  }
+}
+
+template <class T>
+__device__ __forceinline__ void rs_store(void* base, int64_t idx, float v, int dt, int clampf) {
+  if constexpr (std::is_same<T, Dyn>::value) {
+    store_elem(base, idx, v, dt, clampf);
+  } else {
+    store_typed<T>(base, idx, v, clampf);
+  }
+}
+
+template <class T>
+__device__ __forceinline__ void rs_store4(void* base, int64_t idx, const float (&u)[4], int dt,
+                                          int clampf) {
+  if constexpr (std::is_same<T, Dyn>::value) {
+    store4_vec(base, idx, u[0], u[1], u[2], u[3], dt, clampf);
+  } else {
+    store4_typed<T>(base, idx, u[0], u[1], u[2], u[3], clampf);
+  }
+}
+
+// Separable tiled form for output/input spacing ratios down to 1/2 on both
+// axes: a CTA owns RS_TR output rows x RS_TC output columns of one plane.
+//   stage 0  the input window those outputs read (rows i(r0)-1 .. i(r_last)+2,
+//            columns j(c0)-1 .. j(c_last)+2, clamped) decoded into shared memory
+//   pass 1   the column interpolants z(r, k) = w(A(:, k), y_r) of the tile's
+//            rows at every window column (Eq. tensor, first factor)
+//   pass 2   each thread interpolates four consecutive outputs of a row across
+//            the z values (Eq. tensor, second factor) and stores them together
+// Per output this is 1 + (in/out column ratio) + halo 1-D interpolants
+// instead of 5.
 constexpr int RS_TR = 16;
 constexpr int RS_TC = 128;
-constexpr int RS_WC = 2 * RS_TC + 8;
+constexpr int RS_WC = 2 * RS_TC + 8;  // window columns (>= 2 (RS_TC - 1) + 5)
 constexpr int RS_THREADS = 256;
 
-template <int BMODE>
+template <int BMODE, class TIn, class TOut>
 __global__ void __launch_bounds__(RS_THREADS) resample_tiled_kernel(ResampleArgs a, float eps,
                                                                    float beta) {
-  __shared__ float z[RS_TR][RS_WC];
+  extern __shared__ float rs_smem[];
+  float(*win)[RS_WC] = reinterpret_cast<float(*)[RS_WC]>(rs_smem);               // a.win_rows
+  float(*z)[RS_WC] = reinterpret_cast<float(*)[RS_WC]>(rs_smem + a.win_rows * RS_WC);  // RS_TR
   __shared__ int col_j[RS_TC];
   __shared__ float col_t[RS_TC];
+  __shared__ int row_i[RS_TR];
+  __shared__ float row_t[RS_TR];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t c0 = (int64_t)blockIdx.x * RS_TC;
   const int64_t r0 = (int64_t)blockIdx.y * RS_TR;
   const int64_t plane = blockIdx.z;
   const int nc = (int)(a.m_out - c0 < RS_TC ? a.m_out - c0 : RS_TC);
   const int nr = (int)(a.n_out - r0 < RS_TR ? a.n_out - r0 : RS_TR);
-  int64_t jf, jl;
+  int64_t jf, jl, i_first, i_last;
   float tdummy;
   grid_pos(c0, a.m, a.m_out, jf, tdummy);
   grid_pos(c0 + nc - 1, a.m, a.m_out, jl, tdummy);
-  const int64_t kfirst = jf - 1;
-  const int wc = (int)(jl + 2 - kfirst + 1);  // <= RS_WC (host checks the scale)
+  grid_pos(r0, a.n, a.n_out, i_first, tdummy);
+  grid_pos(r0 + nr - 1, a.n, a.n_out, i_last, tdummy);
+  const int64_t kfirst = jf - 1, ifirst = i_first - 1;
+  const int wc = (int)(jl + 2 - kfirst + 1);       // <= RS_WC (host checks the x scale)
+  const int wr = (int)(i_last + 2 - ifirst + 1);   // <= a.win_rows (host sizes it)
   if (tid < nc) {
     int64_t j;
     float t;
@@ -129,55 +173,108 @@ __global__ void __launch_bounds__(RS_THREADS) resample_tiled_kernel(ResampleArgs
     col_j[tid] = (int)(j - 1 - kfirst);
     col_t[tid] = t;
   }
-  const int64_t base = plane * a.in_sc;
-  for (int r = warp; r < nr; r += RS_THREADS / 32) {
+  if (tid >= RS_TC && tid - RS_TC < nr) {
     int64_t i;
-    float ty;
-    grid_pos(r0 + r, a.n, a.n_out, i, ty);
-    int64_t rows[4];
-#pragma unroll
-    for (int p = 0; p < 4; ++p) {
-      const int64_t q = i - 1 + p;
-      rows[p] = base + (q < 0 ? 0 : (q > a.n - 1 ? a.n - 1 : q)) * a.in_sh;
-    }
+    float t;
+    grid_pos(r0 + tid - RS_TC, a.n, a.n_out, i, t);
+    row_i[tid - RS_TC] = (int)(i - 1 - ifirst);
+    row_t[tid - RS_TC] = t;
+  }
+  // stage 0: decoded, clamped input window
+  const int64_t pbase = plane * a.in_sc;
+  for (int rr = warp; rr < wr; rr += RS_THREADS / 32) {
+    int64_t row = ifirst + rr;
+    row = row < 0 ? 0 : (row > a.n - 1 ? a.n - 1 : row);
+    const int64_t rbase = pbase + row * a.in_sh;
     for (int k = lane; k < wc; k += 32) {
-      const int64_t kk = kfirst + k;
-      const int64_t col = (kk < 0 ? 0 : (kk > a.m - 1 ? a.m - 1 : kk)) * a.in_sw;
-      const float v0 = load_elem(a.in, rows[0] + col, a.in_dtype);
-      const float v1 = load_elem(a.in, rows[1] + col, a.in_dtype);
-      const float v2 = load_elem(a.in, rows[2] + col, a.in_dtype);
-      const float v3 = load_elem(a.in, rows[3] + col, a.in_dtype);
-      z[r][k] = weno1d<BMODE>(v0, v1, v2, v3, ty, eps, beta);
+      int64_t col = kfirst + k;
+      col = col < 0 ? 0 : (col > a.m - 1 ? a.m - 1 : col);
+      win[rr][k] = rs_load<TIn>(a.in, rbase + col * a.in_sw, a.in_dtype);
     }
   }
   __syncthreads();
+  // pass 1: column interpolants
   for (int r = warp; r < nr; r += RS_THREADS / 32) {
-    const int64_t orow = plane * a.out_sc + (r0 + r) * a.out_sh;
-    for (int c = lane; c < nc; c += 32) {
-      const int k = col_j[c];
-      const float u = weno1d<BMODE>(z[r][k], z[r][k + 1], z[r][k + 2], z[r][k + 3], col_t[c],
-                                    eps, beta);
-      store_elem(a.out, orow + (c0 + c) * a.out_sw, u, a.out_dtype, a.clamp_float);
+    const int ib = row_i[r];
+    const float ty = row_t[r];
+    for (int k = lane; k < wc; k += 32)
+      z[r][k] = a.n > 1 ? weno1d<BMODE>(win[ib][k], win[ib + 1][k], win[ib + 2][k], win[ib + 3][k],
+                                        ty, eps, beta)
+                        : win[ib + 1][k];
+  }
+  __syncthreads();
+  // pass 2: four consecutive outputs per thread
+  const int c = lane * 4;
+  if (c >= nc) return;
+  const int cn = nc - c < 4 ? nc - c : 4;
+  for (int r = warp; r < nr; r += RS_THREADS / 32) {
+    float u[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (q < cn) {
+        const int k = col_j[c + q];
+        u[q] = a.m > 1 ? weno1d<BMODE>(z[r][k], z[r][k + 1], z[r][k + 2], z[r][k + 3],
+                                       col_t[c + q], eps, beta)
+                       : z[r][k + 1];
+      } else {
+        u[q] = 0.f;
+      }
     }
+    const int64_t o = plane * a.out_sc + (r0 + r) * a.out_sh + (c0 + c) * a.out_sw;
+    if (a.out_vec4 && cn == 4) {
+      rs_store4<TOut>(a.out, o, u, a.out_dtype, a.clamp_float);
+    } else {
+      for (int q = 0; q < cn; ++q)
+        rs_store<TOut>(a.out, o + q * a.out_sw, u[q], a.out_dtype, a.clamp_float);
+    }
+  }
+}
+
+template <int BMODE, class TIn, class TOut>
+cudaError_t launch_tiled(const ResampleArgs& a, float eps, float beta, cudaStream_t stream) {
+  const size_t smem = (size_t)(a.win_rows + RS_TR) * RS_WC * sizeof(float);
+  auto kern = resample_tiled_kernel<BMODE, TIn, TOut>;
+  if (smem > 48 * 1024) {
+    cudaError_t e =
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  const dim3 grid((unsigned)((a.m_out + RS_TC - 1) / RS_TC),
+                  (unsigned)((a.n_out + RS_TR - 1) / RS_TR), (unsigned)a.planes);
+  kern<<<grid, RS_THREADS, smem, stream>>>(a, eps, beta);
+  return cudaGetLastError();
+}
+
+template <class TIn, class TOut>
+cudaError_t launch_tiled_beta(const ResampleArgs& a, float eps, float beta, int bmode,
+                              cudaStream_t stream) {
+  switch (bmode) {
+    case B2: return launch_tiled<B2, TIn, TOut>(a, eps, beta, stream);
+    case B0: return launch_tiled<B0, TIn, TOut>(a, eps, beta, stream);
+    default: return launch_tiled<BGEN, TIn, TOut>(a, eps, beta, stream);
   }
 }
 
 }  // namespace
 
-cudaError_t launch_resample(const ResampleArgs& a, float eps, float beta, int bmode,
+cudaError_t launch_resample(const ResampleArgs& a_in, float eps, float beta, int bmode,
                             cudaStream_t stream) {
-  // the tiled form needs at most RS_WC input columns per tile: column
-  // spacing ratio (m - 1)/(m_out - 1) <= 2
-  const bool tiled = a.m_out == 1 || 2 * (a.m_out - 1) >= (a.m - 1);
+  ResampleArgs a = a_in;
+  // the tiled form reads at most RS_WC window columns and sizes its window
+  // rows from the y ratio: spacing ratios (n - 1)/(n_out - 1) <= 2 per axis
+  const bool tiled = (a.m_out == 1 || 2 * (a.m_out - 1) >= (a.m - 1)) &&
+                     (a.n_out == 1 || 2 * (a.n_out - 1) >= (a.n - 1));
   if (tiled) {
-    const dim3 grid((unsigned)((a.m_out + RS_TC - 1) / RS_TC),
-                    (unsigned)((a.n_out + RS_TR - 1) / RS_TR), (unsigned)a.planes);
-    switch (bmode) {
-      case B2: resample_tiled_kernel<B2><<<grid, RS_THREADS, 0, stream>>>(a, eps, beta); break;
-      case B0: resample_tiled_kernel<B0><<<grid, RS_THREADS, 0, stream>>>(a, eps, beta); break;
-      default: resample_tiled_kernel<BGEN><<<grid, RS_THREADS, 0, stream>>>(a, eps, beta); break;
-    }
-    return cudaGetLastError();
+    a.win_rows = (a.n_out > 1 ? (int)((int64_t)(RS_TR - 1) * (a.n - 1) / (a.n_out - 1)) : 0) + 5;
+    const int i = a.in_dtype, o = a.out_dtype;
+    if (i == DT_U8 && o == DT_U8) return launch_tiled_beta<uint8_t, uint8_t>(a, eps, beta, bmode, stream);
+    if (i == DT_F16 && o == DT_F16) return launch_tiled_beta<__half, __half>(a, eps, beta, bmode, stream);
+    if (i == DT_BF16 && o == DT_BF16)
+      return launch_tiled_beta<__nv_bfloat16, __nv_bfloat16>(a, eps, beta, bmode, stream);
+    if (i == DT_F32 && o == DT_F32) return launch_tiled_beta<float, float>(a, eps, beta, bmode, stream);
+    if (i == DT_U8 && o == DT_F32) return launch_tiled_beta<uint8_t, float>(a, eps, beta, bmode, stream);
+    if (i == DT_F32 && o == DT_U8) return launch_tiled_beta<float, uint8_t>(a, eps, beta, bmode, stream);
+    return launch_tiled_beta<Dyn, Dyn>(a, eps, beta, bmode, stream);
   }
   const dim3 block(32, 8);
   const dim3 grid((unsigned)((a.m_out + 31) / 32), (unsigned)((a.n_out + 7) / 8),

@@ -17,6 +17,9 @@ struct ResampleArgs {
   int64_t in_sc, in_sh, in_sw;
   int64_t out_sc, out_sh, out_sw;
   int clamp_float;
+  int out_vec4;                  // unit column stride, rows and planes of 4-element
+                                 // multiples, 4-element aligned base
+  int win_rows;                  // window rows of the tiled kernel (set by the launcher)
 };
 
 cudaError_t launch_resample(const ResampleArgs& a, float eps, float beta, int bmode,
