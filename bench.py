@@ -66,6 +66,12 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--skip-extras", action="store_true",
                     help="headline only (no fwd+bwd / batched / sweep / cascade)")
+    ap.add_argument("--case", choices=["headline", "resample3x", "fwdbwd"], default="headline",
+                    help="run one secondary workload alone (for profiling) instead of the "
+                         "headline line: resample3x = 1920x1080x3 uint8 -> 5760x3240 tensor "
+                         "WENO; fwdbwd = one autograd step on Bx3x512x512 FP32")
+    ap.add_argument("--batch", type=int, default=32,
+                    help="images per autograd step of --case fwdbwd (the workload has 32)")
     return ap.parse_args()
 
 
@@ -546,8 +552,50 @@ def extras(torch, np, api, scenes, dev, world, hbm_peak):
     return out
 
 
+def run_case(args):
+    """A secondary workload alone: `warmup` untimed then `steps` timed
+    iterations on one GPU; prints one JSON line with the average time."""
+    import numpy as np
+    import torch
+    from paper_2312_00229_gb300 import api, scenes
+    dev = torch.device("cuda")
+    if args.case == "resample3x":
+        hd = torch.from_numpy(scenes.planar(scenes.piecewise_smooth(
+            1080, 1920, seed=scenes.seed_for(2)))).to(dev)
+        o = torch.empty(3, 3240, 5760, dtype=torch.uint8, device=dev)
+        step = lambda: api.resample(hd, 3240, 5760, out=o)
+        work = "1920x1080x3 uint8 -> 5760x3240x3 uint8, tensor WENO"
+    else:
+        xb = np.stack([scenes.planar(scenes.piecewise_smooth(512, 512, scenes.seed_for(5, i),
+                                                             scale_features=True))
+                       for i in range(args.batch)]).astype(np.float32) / 255.0
+        x = torch.from_numpy(xb).to(dev).requires_grad_(True)
+        T = torch.from_numpy(scenes.planar(scenes.piecewise_smooth(
+            1024, 1024, scenes.seed_for(5, 999), scale_features=True)).astype(np.float32) /
+            255.0).to(dev).expand(args.batch, 3, 1024, 1024)
+
+        def step():
+            x.grad = None
+            ((api.zoom2x(x) - T) ** 2).mean().backward()
+        work = f"{args.batch}x3x512x512 FP32 -> 1024x1024, autograd step (forward + adjoint)"
+    for _ in range(max(args.warmup, 1)):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"case": args.case, "workload": work, "steps": args.steps,
+                      "ms_per_step": round(e0.elapsed_time(e1) / max(args.steps, 1), 4)}))
+
+
 def main():
     args = parse_args()
+    if args.case != "headline":
+        run_case(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
