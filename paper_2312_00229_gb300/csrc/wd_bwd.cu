@@ -58,14 +58,22 @@ static_assert(W_END == BWD_ARRAYS, "workspace slot count");
 // samples (lattice 0) or of x points (lattice 1).
 // x: k = 0 (1,1), 1 (-1,-1), 2 (1,-1), 3 (-1,1)
 // E, S: k = 0 (0,1), 1 (0,-1), 2 (1,0), 3 (-1,0)
-__constant__ int c_off[3][4][3][2] = {
-    {{{0, 0}, {1, 1}, {2, 2}}, {{1, 1}, {0, 0}, {-1, -1}},
-     {{0, 1}, {1, 0}, {2, -1}}, {{1, 0}, {0, 1}, {-1, 2}}},
-    {{{0, 0}, {0, 1}, {0, 2}}, {{0, 1}, {0, 0}, {0, -1}},
-     {{-1, 0}, {0, 0}, {1, 0}}, {{0, 0}, {-1, 0}, {-2, 0}}},
-    {{{0, -1}, {0, 0}, {0, 1}}, {{0, 0}, {0, -1}, {0, -2}},
-     {{0, 0}, {1, 0}, {2, 0}}, {{1, 0}, {0, 0}, {-1, 0}}}};
-__constant__ int c_lattice[3][4] = {{0, 0, 0, 0}, {0, 0, 1, 1}, {1, 1, 0, 0}};
+// Compile-time tables: every call site passes literal or unrolled indices,
+// so the lookups fold into immediates.
+__device__ __forceinline__ int off_of(int type, int k, int t, int d) {
+  constexpr int tab[3][4][3][2] = {
+      {{{0, 0}, {1, 1}, {2, 2}}, {{1, 1}, {0, 0}, {-1, -1}},
+       {{0, 1}, {1, 0}, {2, -1}}, {{1, 0}, {0, 1}, {-1, 2}}},
+      {{{0, 0}, {0, 1}, {0, 2}}, {{0, 1}, {0, 0}, {0, -1}},
+       {{-1, 0}, {0, 0}, {1, 0}}, {{0, 0}, {-1, 0}, {-2, 0}}},
+      {{{0, -1}, {0, 0}, {0, 1}}, {{0, 0}, {0, -1}, {0, -2}},
+       {{0, 0}, {1, 0}, {2, 0}}, {{1, 0}, {0, 0}, {-1, 0}}}};
+  return tab[type][k][t][d];
+}
+__device__ __forceinline__ int lattice_of(int type, int k) {
+  constexpr int tab[3][4] = {{0, 0, 0, 0}, {0, 0, 1, 1}, {1, 1, 0, 0}};
+  return tab[type][k];
+}
 
 struct Ctx {
   const float* x;  // input plane
@@ -103,8 +111,8 @@ __device__ __forceinline__ float W0(const Ctx& c, int slot, int I, int J) {
 }
 
 __device__ __forceinline__ float node(const Ctx& c, int type, int k, int t, int a, int b) {
-  const int i = a + c_off[type][k][t][0], j = b + c_off[type][k][t][1];
-  return c_lattice[type][k] == 0 ? Ahat(c, i, j) : W(c, W_X, i, j);
+  const int i = a + off_of(type, k, t, 0), j = b + off_of(type, k, t, 1);
+  return lattice_of(type, k) == 0 ? Ahat(c, i, j) : W(c, W_X, i, j);
 }
 
 struct Pt {
@@ -146,11 +154,12 @@ __device__ __forceinline__ void weights(const float D[4], float beta, float om[4
     const float dmin = fminf(fminf(D[0], D[1]), fminf(D[2], D[3]));
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      const float r = dmin / D[k];
+      const float r = dmin * rcp_approx(D[k]);
       al[k] = BMODE == B2 ? r * r : ex2_approx(beta * lg2_approx(r));
     }
   }
-  const float inv = 1.f / ((al[0] + al[1]) + (al[2] + al[3]));
+  // the largest alpha is 1, so the sum lies in [1, 4]
+  const float inv = rcp_approx((al[0] + al[1]) + (al[2] + al[3]));
 #pragma unroll
   for (int k = 0; k < 4; ++k) om[k] = al[k] * inv;
 }
@@ -172,7 +181,7 @@ __device__ __forceinline__ void point_adjoint(const Pt& q, const float D[4], flo
       acc = fmaf(om[l], fmaf(0.5f, dM, -0.125f * (q.s[kk] - q.s[l])), acc);
     }
     pb[kk] = ub * om[kk];
-    db[kk] = BMODE == B0 ? 0.f : -ub * beta * om[kk] * acc / D[kk];
+    db[kk] = BMODE == B0 ? 0.f : -ub * beta * om[kk] * acc * rcp_approx(D[kk]);
   }
 }
 
@@ -370,10 +379,10 @@ __device__ __forceinline__ float gather(const Ctx& c, int type, int lattice, int
   float acc = 0.f;
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    if (c_lattice[type][k] != lattice) continue;
+    if (lattice_of(type, k) != lattice) continue;
 #pragma unroll
     for (int t = 0; t < 3; ++t)
-      acc += W0(c, co + 3 * k + t, i - c_off[type][k][t][0], j - c_off[type][k][t][1]);
+      acc += W0(c, co + 3 * k + t, i - off_of(type, k, t, 0), j - off_of(type, k, t, 1));
   }
   return acc;
 }
