@@ -165,16 +165,29 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # distributed plumbing (one process per GPU; replicas, no data-path collective)
 # ---------------------------------------------------------------------------
-def dist_setup(n_gpus):
+def dist_setup(n_gpus, backend=None):
+    """Rank, world size and local rank from the launcher's environment; joins
+    the process group when world > 1 (NCCL with a GPU per rank, gloo for the
+    host-only path)."""
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        backend = backend or ("nccl" if torch.cuda.is_available() else "gloo")
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        else:
+            dist.init_process_group(backend)
     return world, rank, local
+
+
+def replica_value(world, steps, out_px_per_step, t_max_s):
+    """Whole-job throughput in Gpix/s: every rank zooms its own frames (weak
+    scaling), timed by the slowest rank."""
+    return world * steps * out_px_per_step / t_max_s / 1e9
 
 
 def barrier(world):
@@ -349,7 +362,7 @@ def run_ours(args):
     clocks = sampler.stop()
     t_local = e0.elapsed_time(e1) / 1e3
     t = max_over_ranks(world, t_local, dev)
-    value = world * steps * OUT_PX / t / 1e9
+    value = replica_value(world, steps, OUT_PX, t)
     per_launch = t_local / steps
 
     pxch = H * W * C
