@@ -299,3 +299,64 @@ def zoom2x_batched(images: Sequence[torch.Tensor], params: Optional[Params] = No
         from . import autotune
         rows_per_tile = autotune.lookup_batched(images, out_dtype, layout)
     return BatchedPlan(images, params, out_dtype, layout, rows_per_tile).run()
+
+
+class HostPipeline:
+    """Zooms a stream of frames that live in (pinned) host memory, overlapping
+    the copy of frame i+1 to the GPU, the zoom of frame i and the copy of
+    frame i-1 back to the host on three CUDA streams, with `depth` device
+    buffer pairs in flight.
+
+        pipe = HostPipeline((3, 1080, 1920), torch.uint8, device="cuda")
+        for x_host, y_host in frames:          # pinned CPU tensors
+            pipe.submit(x_host, y_host)
+        pipe.flush()                           # all y_host written
+
+    `x_host` must stay unchanged and `y_host` unread until flush() (or until
+    `depth` later submissions have been made, when that frame's buffers are
+    reused).  Shapes and dtypes are fixed per pipeline."""
+
+    def __init__(self, in_shape, in_dtype, params: Optional[Params] = None, out_dtype=None,
+                 layout: str = "chw", device="cuda", depth: int = 3):
+        self.params = params or Params()
+        self.layout = layout
+        self.device = torch.device(device)
+        self.depth = int(depth)
+        self.xd = [torch.empty(in_shape, dtype=in_dtype, device=self.device)
+                   for _ in range(self.depth)]
+        self.od = [_out_like(x, self.params, layout, out_dtype or in_dtype) for x in self.xd]
+        self.s_in = torch.cuda.Stream(self.device)
+        self.s_run = torch.cuda.Stream(self.device)
+        self.s_out = torch.cuda.Stream(self.device)
+        ev = lambda: [torch.cuda.Event() for _ in range(self.depth)]
+        self.e_in, self.e_run, self.e_out = ev(), ev(), ev()
+        self.used = [False] * self.depth
+        self.i = 0
+
+    @property
+    def out_shape(self):
+        return tuple(self.od[0].shape)
+
+    def submit(self, x_host: torch.Tensor, y_host: torch.Tensor) -> None:
+        k = self.i % self.depth
+        xd, od = self.xd[k], self.od[k]
+        with torch.cuda.stream(self.s_in):
+            if self.used[k]:
+                self.s_in.wait_event(self.e_run[k])   # xd[k] read by the previous zoom
+            xd.copy_(x_host, non_blocking=True)
+            self.e_in[k].record(self.s_in)
+        with torch.cuda.stream(self.s_run):
+            self.s_run.wait_event(self.e_in[k])
+            if self.used[k]:
+                self.s_run.wait_event(self.e_out[k])  # od[k] copied out
+            zoom2x_fwd(xd, self.params, layout=self.layout, out=od)
+            self.e_run[k].record(self.s_run)
+        with torch.cuda.stream(self.s_out):
+            self.s_out.wait_event(self.e_run[k])
+            y_host.copy_(od, non_blocking=True)
+            self.e_out[k].record(self.s_out)
+        self.used[k] = True
+        self.i += 1
+
+    def flush(self) -> None:
+        self.s_out.synchronize()
