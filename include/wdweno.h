@@ -116,7 +116,8 @@ int weno_zoom2x_bwd(const weno_image* x, const weno_image* grad_out,
 
 /* Scratch bytes weno_zoom2x_bwd needs for an input shaped like `x`
  * (55 FP32 values per cell of the image extended by 6 cells per side, per
- * channel).  Returns 0 for a malformed descriptor. */
+ * channel, the cell count rounded up to a multiple of 4).  Returns 0 for a
+ * malformed descriptor. */
 size_t weno_zoom2x_bwd_workspace_bytes(const weno_image* x);
 
 /* Workspace needed by weno_zoom2x_batched for `count` images (bytes). */

@@ -34,23 +34,28 @@ namespace {
 
 constexpr int G = BWD_GHOST;
 
-// Workspace layout per plane: float arrays of NE x ME cells, one per slot.
-enum Slot {
-  W_XSI = 0,   // 4: phase-1 SIs
-  W_X = 4,     // 1: phase-1 values
-  W_ESI = 5,   // 4: E-point SIs
-  W_SSI = 9,   // 4: S-point SIs
-  W_AB = 13,   // 1: A_bar on the extended grid
-  W_XB = 14,   // 1: X_bar
-  W_EP = 15,   // 4: E p_bar      (phase 1 reuses 15..22 for x p_bar, D_bar)
-  W_ED = 19,   // 4: E D_bar
-  W_SP = 23,   // 4: S p_bar
-  W_SD = 27,   // 4: S D_bar
-  W_ECO = 31,  // 12: E coefficients, index k*3 + t   (phase 1 reuses for x)
-  W_SCO = 43,  // 12: S coefficients
-  W_END = 55
+// Workspace layout per plane (NE x ME cells, the cell count padded to a
+// multiple of 4): seven float4 planes for the four-direction vectors, then
+// scalar planes.
+enum VGroup {
+  G_XSI = 0,  // phase-1 SIs
+  G_ESI = 1,  // E-point SIs
+  G_SSI = 2,  // S-point SIs
+  G_EP = 3,   // E p_bar   (the phase-1 adjoint reuses G_EP, G_ED for x points)
+  G_ED = 4,   // E D_bar
+  G_SP = 5,   // S p_bar
+  G_SD = 6,   // S D_bar
+  G_N = 7
 };
-static_assert(W_END == BWD_ARRAYS, "workspace slot count");
+enum Slot {
+  S_X = 0,     // phase-1 values
+  S_AB = 1,    // A_bar on the extended grid
+  S_XB = 2,    // X_bar
+  S_ECO = 3,   // 12: E coefficients, index k*3 + t   (phase 1 reuses for x)
+  S_SCO = 15,  // 12: S coefficients
+  S_N = 27
+};
+static_assert(4 * G_N + S_N == BWD_ARRAYS, "workspace slot count");
 
 // Point types: 0 = x point X(a,b) (fine (2a+1, 2b+1)), 1 = E point
 // (fine (2a, 2b+1)), 2 = S point (fine (2a+1, 2b)).  For each type and
@@ -81,7 +86,7 @@ struct Ctx {
   int64_t sh, sw;
   float* ws;       // workspace plane
   int NE, ME;
-  int64_t plane_cells;
+  int64_t plane_cells;  // NE * ME rounded up to a multiple of 4
   float w, kap1, kap2, eps1, eps2, beta;
 };
 
@@ -102,17 +107,33 @@ __device__ __forceinline__ int64_t cell(const Ctx& c, int I, int J) {
 }
 
 __device__ __forceinline__ float& W(const Ctx& c, int slot, int I, int J) {
-  return c.ws[slot * c.plane_cells + cell(c, I, J)];
+  return c.ws[(4 * G_N + slot) * c.plane_cells + cell(c, I, J)];
 }
 
 // Workspace value, 0 outside the extended grid.
 __device__ __forceinline__ float W0(const Ctx& c, int slot, int I, int J) {
-  return in_ext(c, I, J) ? c.ws[slot * c.plane_cells + cell(c, I, J)] : 0.f;
+  return in_ext(c, I, J) ? W(c, slot, I, J) : 0.f;
+}
+
+__device__ __forceinline__ float4& V(const Ctx& c, int g, int I, int J) {
+  return reinterpret_cast<float4*>(c.ws)[g * c.plane_cells + cell(c, I, J)];
+}
+
+__device__ __forceinline__ float4 V0(const Ctx& c, int g, int I, int J) {
+  return in_ext(c, I, J) ? V(c, g, I, J) : make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+__device__ __forceinline__ float comp(const float4& v, int d) {
+  return d == 0 ? v.x : (d == 1 ? v.y : (d == 2 ? v.z : v.w));
+}
+
+__device__ __forceinline__ float4 f4(const float a[4]) {
+  return make_float4(a[0], a[1], a[2], a[3]);
 }
 
 __device__ __forceinline__ float node(const Ctx& c, int type, int k, int t, int a, int b) {
   const int i = a + off_of(type, k, t, 0), j = b + off_of(type, k, t, 1);
-  return lattice_of(type, k) == 0 ? Ahat(c, i, j) : W(c, W_X, i, j);
+  return lattice_of(type, k) == 0 ? Ahat(c, i, j) : W(c, S_X, i, j);
 }
 
 struct Pt {
@@ -191,7 +212,7 @@ __device__ __forceinline__ bool setup(const BwdArgs& a, const MethodConsts& k, C
   c.n = (int)a.n; c.m = (int)a.m; c.sh = a.x_sh; c.sw = a.x_sw;
   c.x = a.x + plane * a.x_sc;
   c.NE = c.n + 2 * G; c.ME = c.m + 2 * G;
-  c.plane_cells = (int64_t)c.NE * c.ME;
+  c.plane_cells = ((int64_t)c.NE * c.ME + 3) & ~int64_t(3);
   c.ws = a.ws + plane * (int64_t)BWD_ARRAYS * c.plane_cells;
   c.w = k.w; c.kap1 = k.kappa1; c.kap2 = k.kappa2; c.eps1 = k.eps1; c.eps2 = k.eps2;
   c.beta = k.beta;
@@ -222,16 +243,16 @@ __global__ void k_xsi(BwdArgs a, MethodConsts k) {
 #pragma unroll
     for (int d = 0; d < 4; ++d) si[d] = q.si[d];
   }
-#pragma unroll
-  for (int d = 0; d < 4; ++d) W(c, W_XSI + d, I, J) = si[d];
+  V(c, G_XSI, I, J) = f4(si);
 }
 
 template <int BMODE>
 __device__ __forceinline__ void d_x(const Ctx& c, int I, int J, const float si[4], float D[4]) {
+  const float4 u = V0(c, G_XSI, I - 1, J), v = V0(c, G_XSI, I + 1, J);
+  const float4 l = V0(c, G_XSI, I, J - 1), r = V0(c, G_XSI, I, J + 1);
 #pragma unroll
   for (int d = 0; d < 4; ++d)
-    D[d] = fmaf(c.w, W0(c, W_XSI + d, I - 1, J) + W0(c, W_XSI + d, I + 1, J) +
-                         W0(c, W_XSI + d, I, J - 1) + W0(c, W_XSI + d, I, J + 1), si[d]);
+    D[d] = fmaf(c.w, comp(u, d) + comp(v, d) + comp(l, d) + comp(r, d), si[d]);
 }
 
 template <int BMODE>
@@ -246,7 +267,7 @@ __global__ void k_xval(BwdArgs a, MethodConsts k) {
     weights<BMODE>(D, c.beta, om);
     v = om[0] * q.p[0] + om[1] * q.p[1] + om[2] * q.p[2] + om[3] * q.p[3];
   }
-  W(c, W_X, I, J) = v;
+  W(c, S_X, I, J) = v;
 }
 
 __global__ void k_psi(BwdArgs a, MethodConsts k) {
@@ -259,11 +280,8 @@ __global__ void k_psi(BwdArgs a, MethodConsts k) {
 #pragma unroll
     for (int d = 0; d < 4; ++d) { e[d] = qe.si[d]; s[d] = qs.si[d]; }
   }
-#pragma unroll
-  for (int d = 0; d < 4; ++d) {
-    W(c, W_ESI + d, I, J) = e[d];
-    W(c, W_SSI + d, I, J) = s[d];
-  }
+  V(c, G_ESI, I, J) = f4(e);
+  V(c, G_SSI, I, J) = f4(s);
 }
 
 // ---- phase-2 adjoint ------------------------------------------------------------
@@ -281,60 +299,69 @@ __global__ void k_padj(BwdArgs a, MethodConsts k) {
       // E(a,b): D reads S at (a-1,b), (a,b), (a-1,b+1), (a,b+1)
       const Pt q = eval_pt(c, 1, I, J);
       float D[4];
+      const float4 n0 = V(c, G_SSI, I - 1, J), n1 = V(c, G_SSI, I, J);
+      const float4 n2 = V(c, G_SSI, I - 1, J + 1), n3 = V(c, G_SSI, I, J + 1);
+      const float4 own = V(c, G_ESI, I, J);
 #pragma unroll
       for (int d = 0; d < 4; ++d)
-        D[d] = fmaf(c.w, W(c, W_SSI + d, I - 1, J) + W(c, W_SSI + d, I, J) +
-                             W(c, W_SSI + d, I - 1, J + 1) + W(c, W_SSI + d, I, J + 1),
-                    W(c, W_ESI + d, I, J));
+        D[d] = fmaf(c.w, comp(n0, d) + comp(n1, d) + comp(n2, d) + comp(n3, d), comp(own, d));
       point_adjoint<BMODE>(q, D, c.beta, uE, pE, dE);
     }
     if (uS != 0.f) {
       // S(a,b): D reads E at (a,b-1), (a,b), (a+1,b-1), (a+1,b)
       const Pt q = eval_pt(c, 2, I, J);
       float D[4];
+      const float4 n0 = V(c, G_ESI, I, J - 1), n1 = V(c, G_ESI, I, J);
+      const float4 n2 = V(c, G_ESI, I + 1, J - 1), n3 = V(c, G_ESI, I + 1, J);
+      const float4 own = V(c, G_SSI, I, J);
 #pragma unroll
       for (int d = 0; d < 4; ++d)
-        D[d] = fmaf(c.w, W(c, W_ESI + d, I, J - 1) + W(c, W_ESI + d, I, J) +
-                             W(c, W_ESI + d, I + 1, J - 1) + W(c, W_ESI + d, I + 1, J),
-                    W(c, W_SSI + d, I, J));
+        D[d] = fmaf(c.w, comp(n0, d) + comp(n1, d) + comp(n2, d) + comp(n3, d), comp(own, d));
       point_adjoint<BMODE>(q, D, c.beta, uS, pS, dS);
     }
   }
-#pragma unroll
-  for (int d = 0; d < 4; ++d) {
-    W(c, W_EP + d, I, J) = pE[d];
-    W(c, W_ED + d, I, J) = dE[d];
-    W(c, W_SP + d, I, J) = pS[d];
-    W(c, W_SD + d, I, J) = dS[d];
-  }
+  V(c, G_EP, I, J) = f4(pE);
+  V(c, G_ED, I, J) = f4(dE);
+  V(c, G_SP, I, J) = f4(pS);
+  V(c, G_SD, I, J) = f4(dS);
 }
 
-// SI_bar of direction k at a point: its own D_bar plus w times the D_bar of
-// the points whose D reads it.
-__device__ __forceinline__ float si_bar(const Ctx& c, int type, int k, int a, int b, int dX,
-                                        int dE, int dS) {
+// SI_bar of the four directions at a point: its own D_bar plus w times the
+// D_bar of the points whose D reads it (gX, gE, gS: the D_bar groups).
+__device__ __forceinline__ void si_bar4(const Ctx& c, int type, int a, int b, int gX, int gE,
+                                        int gS, float sb[4]) {
+  float4 own, n0, n1, n2, n3;
   if (type == 0) {
-    return W0(c, dX + k, a, b) + c.w * (W0(c, dX + k, a - 1, b) + W0(c, dX + k, a + 1, b) +
-                                        W0(c, dX + k, a, b - 1) + W0(c, dX + k, a, b + 1));
+    own = V0(c, gX, a, b);
+    n0 = V0(c, gX, a - 1, b); n1 = V0(c, gX, a + 1, b);
+    n2 = V0(c, gX, a, b - 1); n3 = V0(c, gX, a, b + 1);
   } else if (type == 1) {  // E(a,b) is read by S(a,b), S(a,b+1), S(a-1,b), S(a-1,b+1)
-    return W0(c, dE + k, a, b) + c.w * (W0(c, dS + k, a, b) + W0(c, dS + k, a, b + 1) +
-                                        W0(c, dS + k, a - 1, b) + W0(c, dS + k, a - 1, b + 1));
+    own = V0(c, gE, a, b);
+    n0 = V0(c, gS, a, b); n1 = V0(c, gS, a, b + 1);
+    n2 = V0(c, gS, a - 1, b); n3 = V0(c, gS, a - 1, b + 1);
   } else {  // S(a,b) is read by E(a,b), E(a+1,b), E(a,b-1), E(a+1,b-1)
-    return W0(c, dS + k, a, b) + c.w * (W0(c, dE + k, a, b) + W0(c, dE + k, a + 1, b) +
-                                        W0(c, dE + k, a, b - 1) + W0(c, dE + k, a + 1, b - 1));
+    own = V0(c, gS, a, b);
+    n0 = V0(c, gE, a, b); n1 = V0(c, gE, a + 1, b);
+    n2 = V0(c, gE, a, b - 1); n3 = V0(c, gE, a + 1, b - 1);
   }
+#pragma unroll
+  for (int d = 0; d < 4; ++d)
+    sb[d] = comp(own, d) + c.w * (comp(n0, d) + comp(n1, d) + comp(n2, d) + comp(n3, d));
 }
 
-// Node coefficients of every stencil of `type` at (I, J), stored at
-// co + k*3 + t.
-__device__ __forceinline__ void coef_point(const Ctx& c, int type, int I, int J, int pB, int dX,
-                                           int dE, int dS, int co) {
+// Node coefficients of every stencil of `type` at (I, J), stored at scalar
+// slot co + k*3 + t (gP: the p_bar group; gX, gE, gS: the D_bar groups).
+__device__ __forceinline__ void coef_point(const Ctx& c, int type, int I, int J, int gP, int gX,
+                                           int gE, int gS, int co) {
   const float kap = type == 0 ? c.kap1 : c.kap2;
   const float k2 = kap * kap;
+  const float4 pb4 = V(c, gP, I, J);
+  float sb[4];
+  si_bar4(c, type, I, J, gX, gE, gS, sb);
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    const float pbar = W(c, pB + k, I, J);
-    const float sbar = si_bar(c, type, k, I, J, dX, dE, dS);
+    const float pbar = comp(pb4, k);
+    const float sbar = sb[k];
     float c0 = 0.f, c1 = 0.f, c2 = 0.f;
     if (pbar != 0.f || sbar != 0.f) {
       const float n0 = node(c, type, k, 0, I, J);
@@ -360,16 +387,16 @@ __global__ void k_coef2(BwdArgs a, MethodConsts k) {
   const bool e_live = I >= 0 && I <= c.n && J >= -1 && J < c.m;
   const bool s_live = I >= -1 && I < c.n && J >= 0 && J <= c.m;
   if (e_live) {
-    coef_point(c, 1, I, J, W_EP, 0, W_ED, W_SD, W_ECO);
+    coef_point(c, 1, I, J, G_EP, 0, G_ED, G_SD, S_ECO);
   } else {
 #pragma unroll
-    for (int q = 0; q < 12; ++q) W(c, W_ECO + q, I, J) = 0.f;
+    for (int q = 0; q < 12; ++q) W(c, S_ECO + q, I, J) = 0.f;
   }
   if (s_live) {
-    coef_point(c, 2, I, J, W_SP, 0, W_ED, W_SD, W_SCO);
+    coef_point(c, 2, I, J, G_SP, 0, G_ED, G_SD, S_SCO);
   } else {
 #pragma unroll
-    for (int q = 0; q < 12; ++q) W(c, W_SCO + q, I, J) = 0.f;
+    for (int q = 0; q < 12; ++q) W(c, S_SCO + q, I, J) = 0.f;
   }
 }
 
@@ -391,14 +418,14 @@ __global__ void k_gather2(BwdArgs a, MethodConsts k) {
   Ctx c; int I, J;
   if (!setup(a, k, c, I, J)) return;
   const int64_t plane = blockIdx.z;
-  float xb = gather(c, 1, 1, I, J, W_ECO) + gather(c, 2, 1, I, J, W_SCO);
-  float ab = gather(c, 1, 0, I, J, W_ECO) + gather(c, 2, 0, I, J, W_SCO);
+  float xb = gather(c, 1, 1, I, J, S_ECO) + gather(c, 2, 1, I, J, S_SCO);
+  float ab = gather(c, 1, 0, I, J, S_ECO) + gather(c, 2, 0, I, J, S_SCO);
   if (I >= 0 && I < c.n && J >= 0 && J < c.m) {
     xb += gout_at(a, plane, 2 * (int64_t)I + 1, 2 * (int64_t)J + 1);
     ab += gout_at(a, plane, 2 * (int64_t)I, 2 * (int64_t)J);
   }
-  W(c, W_XB, I, J) = xb;
-  W(c, W_AB, I, J) = ab;
+  W(c, S_XB, I, J) = xb;
+  W(c, S_AB, I, J) = ab;
 }
 
 // ---- phase-1 adjoint ----------------------------------------------------------
@@ -407,35 +434,32 @@ __global__ void k_xadj(BwdArgs a, MethodConsts k) {
   Ctx c; int I, J;
   if (!setup(a, k, c, I, J)) return;
   float pX[4] = {0.f, 0.f, 0.f, 0.f}, dX[4] = {0.f, 0.f, 0.f, 0.f};
-  const float xb = W(c, W_XB, I, J);
+  const float xb = W(c, S_XB, I, J);
   if (xb != 0.f && I >= -4 && I < c.n + 4 && J >= -4 && J < c.m + 4) {
     const Pt q = eval_pt(c, 0, I, J);
     float D[4];
     d_x<BMODE>(c, I, J, q.si, D);
     point_adjoint<BMODE>(q, D, c.beta, xb, pX, dX);
   }
-#pragma unroll
-  for (int d = 0; d < 4; ++d) {
-    W(c, W_EP + d, I, J) = pX[d];  // slots reused for x points
-    W(c, W_ED + d, I, J) = dX[d];
-  }
+  V(c, G_EP, I, J) = f4(pX);  // groups reused for x points
+  V(c, G_ED, I, J) = f4(dX);
 }
 
 __global__ void k_coef1(BwdArgs a, MethodConsts k) {
   Ctx c; int I, J;
   if (!setup(a, k, c, I, J)) return;
   if (I >= -5 && I < c.n + 5 && J >= -5 && J < c.m + 5) {
-    coef_point(c, 0, I, J, W_EP, W_ED, 0, 0, W_ECO);
+    coef_point(c, 0, I, J, G_EP, G_ED, 0, 0, S_ECO);
   } else {
 #pragma unroll
-    for (int q = 0; q < 12; ++q) W(c, W_ECO + q, I, J) = 0.f;
+    for (int q = 0; q < 12; ++q) W(c, S_ECO + q, I, J) = 0.f;
   }
 }
 
 __global__ void k_gather1(BwdArgs a, MethodConsts k) {
   Ctx c; int I, J;
   if (!setup(a, k, c, I, J)) return;
-  W(c, W_AB, I, J) += gather(c, 0, 0, I, J, W_ECO);
+  W(c, S_AB, I, J) += gather(c, 0, 0, I, J, S_ECO);
 }
 
 // grad_in(i, j) = sum of A_bar over the extended cells that clamp to (i, j).
@@ -447,7 +471,7 @@ __global__ void k_fold(BwdArgs a, MethodConsts k) {
   const int j0 = J == 0 ? -G : J, j1 = J == c.m - 1 ? c.m - 1 + G : J;
   float acc = 0.f;
   for (int ii = i0; ii <= i1; ++ii)
-    for (int jj = j0; jj <= j1; ++jj) acc += W(c, W_AB, ii, jj);
+    for (int jj = j0; jj <= j1; ++jj) acc += W(c, S_AB, ii, jj);
   const int64_t plane = blockIdx.z;
   a.gin[plane * a.gi_sc + (int64_t)I * a.gi_sh + (int64_t)J * a.gi_sw] = acc;
 }
@@ -473,8 +497,9 @@ cudaError_t launch_all(const BwdArgs& a, const MethodConsts& k, cudaStream_t st)
 }  // namespace
 
 size_t bwd_workspace_bytes(int64_t n, int64_t m, int64_t planes) {
-  return sizeof(float) * (size_t)BWD_ARRAYS * (size_t)(n + 2 * G) * (size_t)(m + 2 * G) *
-         (size_t)planes;
+  // per plane: the extended cell count padded to a multiple of 4 (float4 planes)
+  const size_t cells = ((size_t)(n + 2 * G) * (size_t)(m + 2 * G) + 3) & ~(size_t)3;
+  return sizeof(float) * (size_t)BWD_ARRAYS * cells * (size_t)planes;
 }
 
 cudaError_t launch_zoom2x_bwd(const BwdArgs& a, const MethodConsts& k, int bmode,
