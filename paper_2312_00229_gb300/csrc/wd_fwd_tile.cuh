@@ -19,27 +19,29 @@
 // unrolled twice so their indices are compile-time constants).
 //
 // Pipeline of one step s (input row s is published, row s+2 prefetched):
+//   stage 5  (first, from the previous step's stage 4) E(s-6, c) and S(s-7, c)
+//            (Eqs. tezine, IzrazOmega2dRavno, 2dKombinacijaRavno)
 //   stage 1  row s-2  second differences S1/S2 along both diagonals and their
 //                     squared, kappa-scaled forms (columns c, c+1)
 //   stage 2  row s-3  the four phase-1 smoothness indicators (Eq.
 //                     2Dsmoothness) of X(s-3, c) and its interpolant data
 //   stage 3  row s-4  D (Eq. 2DsmoothnessFinal), alpha (Eq. alpha) and the
 //                     blend (Eqs. IzrazOmega2d, 2dKombinacija) -> X(s-4, c)
-//   stage 4  row s-5  phase-2 indicators of E(s-5, c) and S(s-5, c)
-//   stage 5           E(s-5, c) and S(s-6, c) (Eqs. tezine,
-//                     IzrazOmega2dRavno, 2dKombinacijaRavno)
-//   store             fine row 2(s-5): [A, E], fine row 2(s-6)+1: [S, X]
-// Barrier B1 opens the step; barrier B2 separates the exchange of the
-// phase-2 indicator sums inside the step.
+//   stage 4  row s-5  phase-2 indicators of E(s-5, c) and S(s-5, c), their
+//                     row-pair sums published for the neighbours (slot = step
+//                     parity) and the data stage 5 needs carried to step s+1
+//   store             fine row 2(s-6): [A, E], fine row 2(s-7)+1: [S, X]
+// One barrier (B1) opens each step: every shared value a step reads was
+// written in an earlier step, in a slot no thread writes in the same step.
 //
 // Input path.  When the input rows are 16-byte aligned (FwdArgs::in_bulk),
 // thread 0 requests each input row segment of the strip (with its halo)
 // KAHEAD steps ahead as one asynchronous bulk copy into a ring of RING raw
-// rows in shared memory, completing on the slot's mbarrier.  In step s,
-// after barrier B2, every thread waits for row s and decodes its own
-// (clamped) column of it into the float ring (first read in step s+1).  The sweep's barriers do not wait for these copies, unlike
-// register loads issued before them, so the DRAM latency is covered by
-// KAHEAD steps of work.  Other layouts (INB = false) load each row into a
+// rows in shared memory, completing on the slot's mbarrier.  At the end of
+// step s every thread waits for row s and decodes its own (clamped) column of
+// it into the float ring (first read in step s+1).  The sweep's barriers do
+// not wait for these copies, unlike register loads issued before them, so the
+// DRAM latency is covered by KAHEAD steps of work.  Other layouts (INB = false) load each row into a
 // register two steps ahead.
 #pragma once
 
@@ -69,8 +71,9 @@ struct __align__(16) Exchange {
   float X[4][ROW];            // phase-1 values, slot = row & 3, column c at t + 2
   float4 SI[2][THREADS + 2];  // phase-1 SIs (directions A, B, C, D), slot = row & 1,
                               // column c at t + 1
-  float4 VS[THREADS + 2];     // S-point SIs summed over rows r-1, r (column c at t + 1)
-  float4 VE[THREADS + 2];     // E-point SIs summed over rows r-1, r
+  float4 VS[2][THREADS + 2];  // S-point SIs summed over rows r-1, r (column c at t + 1),
+                              // slot = step parity
+  float4 VE[2][THREADS + 2];  // E-point SIs summed over rows r-1, r
   // --- everything above is zeroed at the start of a tile ---
   unsigned char raw[RING][RAW_BYTES];  // bulk-copied input rows, slot = load index % RING
   uint64_t mbar[RING];                 // completion barrier of each slot
@@ -121,6 +124,8 @@ struct Carry {
   float SI[2][4], P[2][4], px[2][6];             // stage 2
   float sXc[2], qXc[2], sVc[2], qVc[2];          // stage 4 column differences
   float SIE[2][4], SIS[2][4], pS[2][6];          // stage 4
+  // stage 4 results that stage 5 uses one step later
+  float DEp[4], DSp[4], pE[6], a5c, x6;
 };
 
 template <int BMODE, class IO, bool INB>
@@ -223,7 +228,7 @@ struct FwdTile {
   __device__ __forceinline__ void step(int s, float& pf, float& pf2, Carry& C) {
     constexpr int Q = PH ^ 1;  // slot written by the previous step
     const int rs = s - a0;
-    if (rs > H + 5) return;  // padding step past the band (uniform)
+    if (rs > H + 6) return;  // padding step past the band (uniform)
     const float w = k.w;
 
     const int j = rs + HALO_L;  // load number of row s (the sweep starts at a0 - 4)
@@ -241,6 +246,35 @@ struct FwdTile {
     } else {
       ex.A[s & 7][t + 2] = cur;
     }
+
+    // ---- stage 5: E(s-6, c) and S(s-7, c) from the previous step's stage 4 --
+    // (E row r is stage-4 row s-6 of step s-1; the S blend's data pS was
+    // written two steps ago, in the slot of this step's parity, which stage 4
+    // below overwrites)
+    if (rs >= 6 && rs <= H + 5) {
+      const float4 v = ex.VS[(s - 1) & 1][t + 2];  // column c+1
+      const float vs[4] = {v.x, v.y, v.z, v.w};
+      float D[4];
+#pragma unroll
+      for (int d = 0; d < 4; ++d) D[d] = fmaf(w, vs[d], C.DEp[d]);
+      const float e = blend4<BMODE>(D[0], D[1], D[2], D[3], C.pE[0], C.pE[1], C.pE[2], C.pE[3],
+                                    C.pE[4], C.pE[5], k.beta);
+      const int rE = s - 6;  // fine row 2 rE: [A, E]
+      if (rE < n && 2 * rE < orows) store_pair(2 * rE, C.a5c, e);
+    }
+    if (rs >= 7) {
+      const float4 v = ex.VE[(s - 1) & 1][t];  // column c-1
+      const float ve[4] = {v.x, v.y, v.z, v.w};
+      float D[4];
+#pragma unroll
+      for (int d = 0; d < 4; ++d) D[d] = fmaf(w, ve[d], C.DSp[d]);
+      const float* p = C.pS[PH];
+      const float sv = blend4<BMODE>(D[0], D[1], D[2], D[3], p[0], p[1], p[2], p[3], p[4], p[5],
+                                     k.beta);
+      const int rS = s - 7;  // fine row 2 rS + 1: [S, X]
+      if (rS < n && 2 * rS + 1 < orows) store_pair(2 * rS + 1, sv, C.x6);
+    }
+
 
     // Input rows s-3, s-2, s-1 at columns c-1..c+2 (index u + 1).
     float a1[4], a2[4], a3[4];
@@ -367,41 +401,24 @@ struct FwdTile {
         DEp[d] = fmaf(w, VS[d], SIE[d]);
         DSp[d] = fmaf(w, VE[d], C.SIS[Q][d]);
       }
-      ex.VS[t + 1] = make_float4(VS[0], VS[1], VS[2], VS[3]);
-      ex.VE[t + 1] = make_float4(VE[0], VE[1], VE[2], VE[3]);
+      ex.VS[s & 1][t + 1] = make_float4(VS[0], VS[1], VS[2], VS[3]);
+      ex.VE[s & 1][t + 1] = make_float4(VE[0], VE[1], VE[2], VE[3]);
+#pragma unroll
+      for (int d = 0; d < 4; ++d) {
+        C.DEp[d] = DEp[d];
+        C.DSp[d] = DSp[d];
+      }
+#pragma unroll
+      for (int d = 0; d < 6; ++d) C.pE[d] = pE[d];
+      C.a5c = a5[1];
+      C.x6 = x6;
     }
 
-    __syncthreads();  // B2
-    if (INB) {
+    if (INB && rs <= H + 5) {
       // input row s (slot s & 7 last held row s-8, last read in step s-3);
       // first read in step s+1, so this wait delays no barrier
       await_row(j);
       ex.A[s & 7][t + 2] = IO::decode(ex.raw[j & (RING - 1)] + own_off, in_dtype);
-    }
-
-    // ---- stage 5: E(s-5, c) and S(s-6, c) -----------------------------------
-    if (rs >= 5 && rs <= H + 4) {
-      const float4 v = ex.VS[t + 2];  // column c+1
-      const float vs[4] = {v.x, v.y, v.z, v.w};
-      float D[4];
-#pragma unroll
-      for (int d = 0; d < 4; ++d) D[d] = fmaf(w, vs[d], DEp[d]);
-      const float e = blend4<BMODE>(D[0], D[1], D[2], D[3], pE[0], pE[1], pE[2], pE[3], pE[4],
-                                    pE[5], k.beta);
-      const int rE = s - 5;  // fine row 2 rE: [A, E]
-      if (rE < n && 2 * rE < orows) store_pair(2 * rE, a5[1], e);
-    }
-    if (rs >= 6) {
-      const float4 v = ex.VE[t];  // column c-1
-      const float ve[4] = {v.x, v.y, v.z, v.w};
-      float D[4];
-#pragma unroll
-      for (int d = 0; d < 4; ++d) D[d] = fmaf(w, ve[d], DSp[d]);
-      const float* p = C.pS[Q];
-      const float sv = blend4<BMODE>(D[0], D[1], D[2], D[3], p[0], p[1], p[2], p[3], p[4], p[5],
-                                     k.beta);
-      const int rS = s - 6;  // fine row 2 rS + 1: [S, X]
-      if (rS < n && 2 * rS + 1 < orows) store_pair(2 * rS + 1, sv, x6);
     }
   }
 
@@ -414,8 +431,9 @@ struct FwdTile {
       for (int i = t; i < (int)(offsetof(Exchange, raw) / sizeof(float)); i += THREADS) z[i] = 0.f;
     }
     const int s_begin = a0 - 4;
-    const int s_end = a0 + H + 5;  // inclusive
-    const int loads = s_end - s_begin + 1;
+    const int s_last = a0 + H + 5;   // last input row of the band's sweep
+    const int s_end = s_last + 1;    // inclusive: one more step finishes stage 5
+    const int loads = s_last - s_begin + 1;
     if (INB && t == 0) {
       for (int i = 0; i < RING; ++i) mbar_init(&ex.mbar[i], 1);
       fence_mbar_init();
@@ -432,6 +450,11 @@ struct FwdTile {
       for (int d = 0; d < 6; ++d) C.px[i][d] = C.pS[i][d] = 0.f;
       C.sXc[i] = C.qXc[i] = C.sVc[i] = C.qVc[i] = 0.f;
     }
+#pragma unroll
+    for (int d = 0; d < 4; ++d) C.DEp[d] = C.DSp[d] = 0.f;
+#pragma unroll
+    for (int d = 0; d < 6; ++d) C.pE[d] = 0.f;
+    C.a5c = C.x6 = 0.f;
     float pf = INB ? 0.f : load_row(s_begin);
     float pf2 = INB ? 0.f : load_row(s_begin + 1);
     for (int s = s_begin; s <= s_end; s += 2) {
