@@ -242,7 +242,7 @@ struct FwdTile {
     __syncthreads();  // B1: rows published in step s-1 are visible
     if (INB) {
       // the slot of load j + KAHEAD was last decoded in step s-2
-      if (t == 0 && rs + KAHEAD <= H + 5) issue_row(j + KAHEAD, s + KAHEAD);
+      if (t == 0 && rs >= -HALO_L && rs + KAHEAD <= H + 5) issue_row(j + KAHEAD, s + KAHEAD);
     } else {
       ex.A[s & 7][t + 2] = cur;
     }
@@ -252,7 +252,7 @@ struct FwdTile {
     // written two steps ago, in the slot of this step's parity, which stage 4
     // below overwrites)
     if (rs >= 6 && rs <= H + 5) {
-      const float4 v = ex.VS[(s - 1) & 1][t + 2];  // column c+1
+      const float4 v = ex.VS[PH ^ 1][t + 2];  // column c+1 (slot of step s-1)
       const float vs[4] = {v.x, v.y, v.z, v.w};
       float D[4];
 #pragma unroll
@@ -263,7 +263,7 @@ struct FwdTile {
       if (rE < n && 2 * rE < orows) store_pair(2 * rE, C.a5c, e);
     }
     if (rs >= 7) {
-      const float4 v = ex.VE[(s - 1) & 1][t];  // column c-1
+      const float4 v = ex.VE[PH ^ 1][t];  // column c-1
       const float ve[4] = {v.x, v.y, v.z, v.w};
       float D[4];
 #pragma unroll
@@ -308,7 +308,7 @@ struct FwdTile {
       SI[1] = fmaf(G1, G1, C.q1[Q][0]);
       SI[2] = fmaf(G2, G2, C.q2[PH][0]);
       SI[3] = fmaf(G2, G2, C.q2[Q][1]);
-      ex.SI[(s - 3) & 1][t + 1] = make_float4(SI[0], SI[1], SI[2], SI[3]);
+      ex.SI[PH ^ 1][t + 1] = make_float4(SI[0], SI[1], SI[2], SI[3]);  // slot (s-3) & 1
 #pragma unroll
       for (int d = 0; d < 4; ++d) C.P[PH][d] = fmaf(w, C.SI[Q][d], SI[d]);
       C.px[PH][0] = a3[1] + a2[2];  // N0 + N1 of the (1,1) diagonal pair
@@ -324,8 +324,8 @@ struct FwdTile {
     // partial P(a) = SI(a) + w SI(a-1) was formed one step earlier.
     float x4 = 0.f;
     if (rs >= 2) {
-      const float4 l = ex.SI[(s - 4) & 1][t];
-      const float4 r = ex.SI[(s - 4) & 1][t + 2];
+      const float4 l = ex.SI[PH][t];  // slot (s-4) & 1
+      const float4 r = ex.SI[PH][t + 2];
       const float hl[4] = {l.x, l.y, l.z, l.w};
       const float hr[4] = {r.x, r.y, r.z, r.w};
       float D[4];
@@ -401,8 +401,8 @@ struct FwdTile {
         DEp[d] = fmaf(w, VS[d], SIE[d]);
         DSp[d] = fmaf(w, VE[d], C.SIS[Q][d]);
       }
-      ex.VS[s & 1][t + 1] = make_float4(VS[0], VS[1], VS[2], VS[3]);
-      ex.VE[s & 1][t + 1] = make_float4(VE[0], VE[1], VE[2], VE[3]);
+      ex.VS[PH][t + 1] = make_float4(VS[0], VS[1], VS[2], VS[3]);
+      ex.VE[PH][t + 1] = make_float4(VE[0], VE[1], VE[2], VE[3]);
 #pragma unroll
       for (int d = 0; d < 4; ++d) {
         C.DEp[d] = DEp[d];
@@ -414,7 +414,7 @@ struct FwdTile {
       C.x6 = x6;
     }
 
-    if (INB && rs <= H + 5) {
+    if (INB && rs >= -HALO_L && rs <= H + 5) {
       // input row s (slot s & 7 last held row s-8, last read in step s-3);
       // first read in step s+1, so this wait delays no barrier
       await_row(j);
@@ -430,14 +430,18 @@ struct FwdTile {
       float* z = reinterpret_cast<float*>(&ex);
       for (int i = t; i < (int)(offsetof(Exchange, raw) / sizeof(float)); i += THREADS) z[i] = 0.f;
     }
-    const int s_begin = a0 - 4;
+    // The sweep starts on an even row, so that step<PH> runs on rows of
+    // parity PH and the parity-slotted rings have compile-time indices; an
+    // odd a0 - 4 adds one leading step in which every stage is idle.
+    const int s_first = a0 - 4;          // first input row the band needs
+    const int s_begin = s_first & ~1;
     const int s_last = a0 + H + 5;   // last input row of the band's sweep
     const int s_end = s_last + 1;    // inclusive: one more step finishes stage 5
-    const int loads = s_last - s_begin + 1;
+    const int loads = s_last - s_first + 1;
     if (INB && t == 0) {
       for (int i = 0; i < RING; ++i) mbar_init(&ex.mbar[i], 1);
       fence_mbar_init();
-      for (int j = 0; j < KAHEAD && j < loads; ++j) issue_row(j, s_begin + j);
+      for (int j = 0; j < KAHEAD && j < loads; ++j) issue_row(j, s_first + j);
     }
     Carry C;
 #pragma unroll
