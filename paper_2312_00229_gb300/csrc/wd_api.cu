@@ -41,7 +41,7 @@ int64_t default_rows_per_band(int64_t n, int64_t m, int64_t planes) {
   const int64_t slots = (int64_t)sms * kFwdCtasPerSm;
   const int64_t strips = (m + tile_width_fwd() - 1) / tile_width_fwd();
   const int64_t base = strips * planes;
-  const int64_t fill = 6;
+  const int64_t fill = 7;  // extra steps per band: 4 + 5 halo rows + 2 pipeline steps
   int64_t best_rpb = n, best_cost = -1;
   for (int64_t bands = 1; bands <= 4096; ++bands) {
     const int64_t rpb = (n + bands - 1) / bands;

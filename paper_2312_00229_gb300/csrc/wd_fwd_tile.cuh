@@ -224,11 +224,14 @@ struct FwdTile {
   }
   __device__ __forceinline__ float own(int r) const { return ex.A[r & 7][t + 2]; }
 
-  template <int PH>
+  // FULL: a step in the middle of the band, where every stage's row is
+  // inside the band (7 <= rs <= H + 4): the stage guards are compiled out so
+  // the whole step is one block for the scheduler.
+  template <int PH, bool FULL>
   __device__ __forceinline__ void step(int s, float& pf, float& pf2, Carry& C) {
     constexpr int Q = PH ^ 1;  // slot written by the previous step
     const int rs = s - a0;
-    if (rs > H + 6) return;  // padding step past the band (uniform)
+    if (!FULL && rs > H + 6) return;  // padding step past the band (uniform)
     const float w = k.w;
 
     const int j = rs + HALO_L;  // load number of row s (the sweep starts at a0 - 4)
@@ -251,7 +254,7 @@ struct FwdTile {
     // (E row r is stage-4 row s-6 of step s-1; the S blend's data pS was
     // written two steps ago, in the slot of this step's parity, which stage 4
     // below overwrites)
-    if (rs >= 6 && rs <= H + 5) {
+    if (FULL || (rs >= 6 && rs <= H + 5)) {
       const float4 v = ex.VS[PH ^ 1][t + 2];  // column c+1 (slot of step s-1)
       const float vs[4] = {v.x, v.y, v.z, v.w};
       float D[4];
@@ -262,7 +265,7 @@ struct FwdTile {
       const int rE = s - 6;  // fine row 2 rE: [A, E]
       if (rE < n && 2 * rE < orows) store_pair(2 * rE, C.a5c, e);
     }
-    if (rs >= 7) {
+    if (FULL || rs >= 7) {
       const float4 v = ex.VE[PH ^ 1][t];  // column c-1
       const float ve[4] = {v.x, v.y, v.z, v.w};
       float D[4];
@@ -284,7 +287,7 @@ struct FwdTile {
 
     // ---- stage 1: diagonal second differences at row s-2, columns c, c+1 --
     // S1(i,j) = A(i-1,j-1) - 2A(i,j) + A(i+1,j+1);  S2 along (1,-1)
-    if (rs >= -1) {
+    if (FULL || rs >= -1) {
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
         C.S1[PH][u] = fmaf(-2.f, a2[u + 1], a3[u] + a1[u + 2]);
@@ -300,7 +303,7 @@ struct FwdTile {
     //   B (-1,-1): nodes A(a+1,b+1), A(a,b),   A(a-1,b-1); s = S1(a,b)
     //   C (1,-1):  nodes A(a,b+1), A(a+1,b),   A(a+2,b-1); s = S2(a+1,b)
     //   D (-1,1):  nodes A(a+1,b), A(a,b+1),   A(a-1,b+2); s = S2(a,b+1)
-    if (rs >= 0) {
+    if (FULL || rs >= 0) {
       const float G1 = a2[2] - a3[1];  // A(a+1,b+1) - A(a,b)
       const float G2 = a2[1] - a3[2];  // A(a+1,b) - A(a,b+1)
       float* SI = C.SI[PH];
@@ -323,7 +326,7 @@ struct FwdTile {
     // D = SI(a) + w (SI(a-1) + SI(a+1) + SI(a, c-1) + SI(a, c+1)), where the
     // partial P(a) = SI(a) + w SI(a-1) was formed one step earlier.
     float x4 = 0.f;
-    if (rs >= 2) {
+    if (FULL || rs >= 2) {
       const float4 l = ex.SI[PH][t];  // slot (s-4) & 1
       const float4 r = ex.SI[PH][t + 2];
       const float hl[4] = {l.x, l.y, l.z, l.w};
@@ -342,14 +345,14 @@ struct FwdTile {
     // The column second difference of A centred at A(r+1) is carried to the
     // next step as the one centred at A(r), so it starts one row early.
     float a5[4] = {0.f, 0.f, 0.f, 0.f}, a4 = 0.f;
-    if (rs >= 3) {
+    if (FULL || rs >= 3) {
       row4(s - 5, a5);
       a4 = own(s - 4);
       C.sVc[PH] = fmaf(-2.f, a4, a5[1] + a3[1]);
       C.qVc[PH] = sq_eps(k.kappa2, C.sVc[PH], k.eps2);
     }
     float DEp[4], DSp[4], pE[6], x6 = 0.f;
-    if (rs >= 4) {
+    if (FULL || rs >= 4) {
       // phase-1 row r at columns c-2..c+1, and column c at row r-1
       const float* xp = ex.X[(s - 5) & 3] + t;
       const float xr0 = xp[0], xr1 = xp[1], xr2 = xp[2], xr3 = xp[3];
@@ -414,7 +417,7 @@ struct FwdTile {
       C.x6 = x6;
     }
 
-    if (INB && rs >= -HALO_L && rs <= H + 5) {
+    if (INB && (FULL || (rs >= -HALO_L && rs <= H + 5))) {
       // input row s (slot s & 7 last held row s-8, last read in step s-3);
       // first read in step s+1, so this wait delays no barrier
       await_row(j);
@@ -461,9 +464,18 @@ struct FwdTile {
     C.a5c = C.x6 = 0.f;
     float pf = INB ? 0.f : load_row(s_begin);
     float pf2 = INB ? 0.f : load_row(s_begin + 1);
-    for (int s = s_begin; s <= s_end; s += 2) {
-      step<0>(s, pf, pf2, C);
-      step<1>(s + 1, pf, pf2, C);
+    int s = s_begin;
+    for (; s <= s_end && s - a0 < 7; s += 2) {  // pipeline fill
+      step<0, false>(s, pf, pf2, C);
+      step<1, false>(s + 1, pf, pf2, C);
+    }
+    for (; s + 1 - a0 <= H + 4; s += 2) {  // every stage inside the band
+      step<0, true>(s, pf, pf2, C);
+      step<1, true>(s + 1, pf, pf2, C);
+    }
+    for (; s <= s_end; s += 2) {  // drain
+      step<0, false>(s, pf, pf2, C);
+      step<1, false>(s + 1, pf, pf2, C);
     }
     if (INB) {
       __syncthreads();  // every thread has decoded its last row
