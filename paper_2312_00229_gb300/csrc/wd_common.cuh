@@ -26,8 +26,7 @@ namespace wdweno {
 enum DType { DT_U8 = 0, DT_F16 = 1, DT_BF16 = 2, DT_F32 = 3 };
 
 // How Eq. (alpha) is evaluated.
-//   B2  : beta == 2, alpha = 1 / D^2 (D already holds eps_h), with a
-//         scale-free fallback when that leaves the FP32 range.
+//   B2  : beta == 2, alpha = (D_min / D)^2 (D already holds eps_h).
 //   BGEN: any beta > 0, alpha = (D_min / D)^beta (scale-free).
 //   B0  : beta == 0, all weights equal.
 enum BetaMode { B2 = 0, BGEN = 1, B0 = 2 };
@@ -312,14 +311,9 @@ __device__ __forceinline__ float blend4(float D0, float D1, float D2, float D3, 
   if (BMODE == B0) {
     return combine(1.f, 1.f, 1.f, 1.f, M01, M23, s0, s1, s2, s3, 0.125f);
   } else if (BMODE == B2) {
-    float a0 = rcp_approx(D0 * D0), a1 = rcp_approx(D1 * D1);
-    float a2 = rcp_approx(D2 * D2), a3 = rcp_approx(D3 * D3);
-    float den = (a0 + a1) + (a2 + a3);
-    // D^2 left the normal FP32 range (tiny eps_h or huge data): use the
-    // scale-free form of the same weights.
-    if (!(den > 0.0f && den < 3.0e38f))
-      return blend_scale_free(D0, D1, D2, D3, M01, M23, s0, s1, s2, s3, 2.0f);
-    return combine(a0, a1, a2, a3, M01, M23, s0, s1, s2, s3, rcp_approx(den + den));
+    // alpha_k = (D_min / D_k)^2: the same weights as 1 / D_k^2 up to a common
+    // factor, in range for any data magnitude, and without a branch
+    return blend_scale_free(D0, D1, D2, D3, M01, M23, s0, s1, s2, s3, 2.0f);
   } else {
     return blend_scale_free(D0, D1, D2, D3, M01, M23, s0, s1, s2, s3, beta);
   }

@@ -225,8 +225,9 @@ struct FwdTile {
   __device__ __forceinline__ float own(int r) const { return ex.A[r & 7][t + 2]; }
 
   // FULL: a step in the middle of the band, where every stage's row is
-  // inside the band (7 <= rs <= H + 4): the stage guards are compiled out so
-  // the whole step is one block for the scheduler.
+  // inside the band (7 <= rs <= H + 4) and every stored row inside the
+  // output: the guards are compiled out so the whole step is one block for
+  // the scheduler.
   template <int PH, bool FULL>
   __device__ __forceinline__ void step(int s, float& pf, float& pf2, Carry& C) {
     constexpr int Q = PH ^ 1;  // slot written by the previous step
@@ -263,7 +264,7 @@ struct FwdTile {
       const float e = blend4<BMODE>(D[0], D[1], D[2], D[3], C.pE[0], C.pE[1], C.pE[2], C.pE[3],
                                     C.pE[4], C.pE[5], k.beta);
       const int rE = s - 6;  // fine row 2 rE: [A, E]
-      if (rE < n && 2 * rE < orows) store_pair(2 * rE, C.a5c, e);
+      if (FULL || (rE < n && 2 * rE < orows)) store_pair(2 * rE, C.a5c, e);
     }
     if (FULL || rs >= 7) {
       const float4 v = ex.VE[PH ^ 1][t];  // column c-1
@@ -275,7 +276,7 @@ struct FwdTile {
       const float sv = blend4<BMODE>(D[0], D[1], D[2], D[3], p[0], p[1], p[2], p[3], p[4], p[5],
                                      k.beta);
       const int rS = s - 7;  // fine row 2 rS + 1: [S, X]
-      if (rS < n && 2 * rS + 1 < orows) store_pair(2 * rS + 1, sv, C.x6);
+      if (FULL || (rS < n && 2 * rS + 1 < orows)) store_pair(2 * rS + 1, sv, C.x6);
     }
 
 
@@ -469,7 +470,8 @@ struct FwdTile {
       step<0, false>(s, pf, pf2, C);
       step<1, false>(s + 1, pf, pf2, C);
     }
-    for (; s + 1 - a0 <= H + 4; s += 2) {  // every stage inside the band
+    // every stage's row inside the band, every stored row inside the output
+    for (; s + 1 - a0 <= H + 4 && s + 1 <= n + 5; s += 2) {
       step<0, true>(s, pf, pf2, C);
       step<1, true>(s + 1, pf, pf2, C);
     }
