@@ -372,7 +372,7 @@ def run_ours(args):
     roofline = {"bound": "alu", "achieved": round(achieved_ops / 1e12, 3),
                 "peak": round(alu_peak / 1e12, 3), "unit": "Top/s",
                 "frac": round(achieved_ops / alu_peak, 4), "traffic": traffic,
-                "kernel": "zoom2x_fwd_kernel<B2, u8->u8>",
+                "kernel": "zoom2x_fwd_kernel<B2R, u8->u8>",
                 "ops_per_pxch": ALGO_FP32_OPS_PER_PXCH,
                 "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_max_mhz:.0f} MHz",
                 "hbm": {"achieved": round(achieved_gbs, 1), "peak": hbm_peak, "unit": "GB/s",

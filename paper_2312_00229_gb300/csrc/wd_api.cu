@@ -125,6 +125,37 @@ bool fold_consts(const weno_params& p, MethodConsts* k, int* bmode) {
   return true;
 }
 
+// Whether the forward kernels may take the beta = 2 weights of Eq. (alpha)
+// as 1 / D^2 directly (B2R) instead of the scale-free (D_min / D)^2.  That
+// needs every D inside [lo, hi] with 1/hi^2 and 1/lo^2 normal FP32 numbers,
+// and the weight sum and the blend numerator finite.  The storage type
+// bounds the data: |input| <= v0 (uint8 decodes to [0, 1]; FP16 <= 65504).
+// Every node of an interpolant is an input or a phase-1 value, a convex
+// combination of quadratic interpolants (|p| <= 1.25 max |node|), so
+// |node| <= v = 1.25 v0; then |g| <= 2v, |s| <= 4v and
+//   SI <= 4 v^2 + (25/12) 16 v^2 + eps_h,  D <= (1 + 4w) SI_max,
+//   D >= eps_h / sqrt(2) (phase 2 of the literal SI scaling; eps_h otherwise).
+// The weights are at most 1/lo^2 each, the numerator at most 16 v times their
+// largest value.  BFloat16 and FP32 data are unbounded: they keep B2.
+bool direct_b2_ok(const weno_params& p, int in_t) {
+  double v0;
+  if (in_t == WENO_U8) {
+    v0 = 1.0;
+  } else if (in_t == WENO_F16) {
+    v0 = 65504.0;
+  } else {
+    return false;
+  }
+  const double h = p.h, w = h * h / 4.0, eps_h = double(p.k_eps) * h * h;
+  const double v = 1.25 * v0 * (1.0 + 1e-3);  // slack for the approximate reciprocals
+  const double si_max = 4.0 * v * v + 25.0 / 12.0 * 16.0 * v * v + eps_h;
+  const double hi = (1.0 + 4.0 * w) * si_max;
+  const double lo = eps_h / 2.0;
+  if (!(lo >= 1e-18) || !(hi <= 1e18)) return false;
+  const double a_max = 1.0 / (lo * lo);
+  return 8.0 * a_max <= 1e37 && 16.0 * v * a_max <= 1e37;
+}
+
 int check_pair(const weno_image* in, int in_t, const weno_image* out, int out_t,
                const weno_params& p, int64_t* orows, int64_t* ocols) {
   if (!image_ok(in) || !image_ok(out)) return WENO_EINVAL;
@@ -209,6 +240,7 @@ int weno_zoom2x_fwd_tiled(const weno_image* in, weno_dtype in_t, const weno_imag
   const int64_t rpb = rows_per_tile > 0 ? rows_per_tile
                                         : default_rows_per_band(in->height, in->width,
                                                                 in->channels);
+  if (bmode == B2 && direct_b2_ok(p, in_t)) bmode = B2R;
   FwdArgs a = make_fwd_args(in, in_t, out, out_t, orows, ocols, rpb);
   if ((a.n + rpb - 1) / rpb > 65535) return WENO_ERANGE;
   cudaError_t e = launch_zoom2x_fwd(a, k, bmode, static_cast<cudaStream_t>(stream));
@@ -282,6 +314,7 @@ int weno_zoom2x_batched(int count, const weno_image* d_in, weno_dtype in_t,
   MethodConsts k;
   int bmode;
   if (!fold_consts(p, &k, &bmode)) return WENO_EINVAL;
+  if (bmode == B2 && direct_b2_ok(p, in_t)) bmode = B2R;
   BatchedArgs a;
   a.count = count;
   a.in = d_in;

@@ -29,7 +29,10 @@ enum DType { DT_U8 = 0, DT_F16 = 1, DT_BF16 = 2, DT_F32 = 3 };
 //   B2  : beta == 2, alpha = (D_min / D)^2 (D already holds eps_h).
 //   BGEN: any beta > 0, alpha = (D_min / D)^beta (scale-free).
 //   B0  : beta == 0, all weights equal.
-enum BetaMode { B2 = 0, BGEN = 1, B0 = 2 };
+//   B2R : beta == 2, alpha = 1 / D^2 as written; chosen by the host only
+//         where the storage type bounds the data so that every weight, their
+//         sum and the blend numerator stay inside the normal FP32 range.
+enum BetaMode { B2 = 0, BGEN = 1, B0 = 2, B2R = 3 };
 
 // Constants of the method folded for the kernels.  eps_h is spread over the
 // five smoothness indicators that form each D (Eqs. 2DsmoothnessFinal and
@@ -141,10 +144,14 @@ __device__ __forceinline__ float load_elem(const void* base, int64_t idx, int dt
   }
 }
 
-__device__ __forceinline__ uint32_t encode_u8(float v) {
-  // saturate, scale, round half to even
-  return __float2uint_rn(__saturatef(v) * 255.0f);
+// saturate, scale, round half to even: adding 1.5 * 2^23 inside the FMA
+// leaves a float whose unit in the last place is 1, so its low mantissa byte
+// is the code, from one rounding of the exact product.
+__device__ __forceinline__ uint32_t encode_u8_bits(float v) {
+  return __float_as_uint(fmaf(__saturatef(v), 255.0f, 12582912.0f));
 }
+
+__device__ __forceinline__ uint32_t encode_u8(float v) { return encode_u8_bits(v) & 0xFFu; }
 
 __device__ __forceinline__ float clamp_opt(float v, int clampf) {
   return clampf ? __saturatef(v) : v;
@@ -173,8 +180,9 @@ __device__ __forceinline__ void store4_vec(void* base, int64_t idx, float v0, fl
                                            float v3, int dt, int clampf) {
   switch (dt) {
     case DT_U8: {
-      uint32_t packed = encode_u8(v0) | (encode_u8(v1) << 8) | (encode_u8(v2) << 16) |
-                        (encode_u8(v3) << 24);
+      const uint32_t lo = __byte_perm(encode_u8_bits(v0), encode_u8_bits(v1), 0x0040);
+      const uint32_t hi = __byte_perm(encode_u8_bits(v2), encode_u8_bits(v3), 0x0040);
+      const uint32_t packed = __byte_perm(lo, hi, 0x5410);
       *reinterpret_cast<uint32_t*>(static_cast<uint8_t*>(base) + idx) = packed;
       break;
     }
@@ -211,7 +219,8 @@ __device__ __forceinline__ void store2_vec(void* base, int64_t idx, float v0, fl
                                            int clampf) {
   switch (dt) {
     case DT_U8: {
-      const uint16_t packed = (uint16_t)(encode_u8(v0) | (encode_u8(v1) << 8));
+      const uint16_t packed =
+          (uint16_t)__byte_perm(encode_u8_bits(v0), encode_u8_bits(v1), 0x0040);
       *reinterpret_cast<uint16_t*>(static_cast<uint8_t*>(base) + idx) = packed;
       break;
     }
@@ -314,6 +323,11 @@ __device__ __forceinline__ float blend4(float D0, float D1, float D2, float D3, 
     // alpha_k = (D_min / D_k)^2: the same weights as 1 / D_k^2 up to a common
     // factor, in range for any data magnitude, and without a branch
     return blend_scale_free(D0, D1, D2, D3, M01, M23, s0, s1, s2, s3, 2.0f);
+  } else if (BMODE == B2R) {
+    const float a0 = rcp_approx(D0 * D0), a1 = rcp_approx(D1 * D1);
+    const float a2 = rcp_approx(D2 * D2), a3 = rcp_approx(D3 * D3);
+    const float den = (a0 + a1) + (a2 + a3);
+    return combine(a0, a1, a2, a3, M01, M23, s0, s1, s2, s3, rcp_approx(den + den));
   } else {
     return blend_scale_free(D0, D1, D2, D3, M01, M23, s0, s1, s2, s3, beta);
   }

@@ -6,8 +6,8 @@
 
 namespace wdweno {
 
-cudaError_t launch_fwd_typed(const FwdArgs& a, const MethodConsts& k, cudaStream_t stream,
-                             bool* handled);
+cudaError_t launch_fwd_typed(const FwdArgs& a, const MethodConsts& k, int bmode,
+                             cudaStream_t stream, bool* handled);
 
 int tile_width_fwd() { return fwd_tile::TILE_W; }
 int threads_fwd() { return fwd_tile::THREADS; }
@@ -15,10 +15,11 @@ int threads_fwd() { return fwd_tile::THREADS; }
 cudaError_t launch_zoom2x_fwd(const FwdArgs& a, const MethodConsts& k, int bmode,
                               cudaStream_t stream) {
   using fwd_tile::DynIO;
-  if (bmode == B2) {
+  if (bmode == B2 || bmode == B2R) {
     bool handled = false;
-    cudaError_t e = launch_fwd_typed(a, k, stream, &handled);
+    cudaError_t e = launch_fwd_typed(a, k, bmode, stream, &handled);
     if (handled) return e;
+    if (bmode == B2R) return fwd_kernels::launch_fwd<B2R, DynIO>(a, k, stream);
     return fwd_kernels::launch_fwd<B2, DynIO>(a, k, stream);
   }
   if (bmode == B0) return fwd_kernels::launch_fwd<B0, DynIO>(a, k, stream);

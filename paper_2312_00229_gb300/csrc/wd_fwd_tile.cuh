@@ -14,7 +14,9 @@
 // Shared memory holds rings of recent rows that neighbouring columns read:
 // the decoded input rows (8), the phase-1 values (4), the phase-1
 // smoothness indicators (2) and the row-pair sums of the phase-2
-// indicators.  Registers hold only values a thread carries for its own
+// indicators.  The input and phase-1 rings repeat their first slots after
+// the last, so the rows a step reads are at constant offsets from one slot
+// address.  Registers hold only values a thread carries for its own
 // column from one step to the next (period-2 rings; the step loop is
 // unrolled twice so their indices are compile-time constants).
 //
@@ -59,16 +61,19 @@ constexpr int TILE_W = THREADS - 9;  // output columns per CTA
 constexpr int ROW = THREADS + 4;     // floats per staged row (2 pad each side)
 constexpr int RING = 8;              // raw input rows in flight or in use
 constexpr int KAHEAD = 6;            // rows requested ahead of the sweep (< RING)
-// Raw bytes of one strip row: 256 FP32 columns plus up to 16 bytes of
-// alignment slack at each end.
-constexpr int RAW_BYTES = THREADS * 4 + 32;
+// Raw bytes of one strip row: 256 columns of 1- or 2-byte storage (the only
+// sizes taken by bulk copy) plus up to 16 bytes of alignment slack at each end.
+constexpr int RAW_BYTES = THREADS * 2 + 32;
 // Bound on one wait for an input row (nanoseconds of global time).
 constexpr unsigned long long WAIT_LIMIT_NS = 1000000000ull;
 static_assert(KAHEAD < RING && (RING & (RING - 1)) == 0, "input ring shape");
 
 struct __align__(16) Exchange {
-  float A[8][ROW];            // input rows, slot = row & 7, column c at t + 2
-  float X[4][ROW];            // phase-1 values, slot = row & 3, column c at t + 2
+  float A[12][ROW];           // input rows, slot = row & 7, column c at t + 2; slots
+                              // 8..11 repeat 0..3 so five consecutive rows are
+                              // at consecutive slots from any start
+  float X[5][ROW];            // phase-1 values, slot = row & 3, column c at t + 2; slot
+                              // 4 repeats 0
   float4 SI[2][THREADS + 2];  // phase-1 SIs (directions A, B, C, D), slot = row & 1,
                               // column c at t + 1
   float4 VS[2][THREADS + 2];  // S-point SIs summed over rows r-1, r (column c at t + 1),
@@ -79,6 +84,7 @@ struct __align__(16) Exchange {
   uint64_t mbar[RING];                 // completion barrier of each slot
 };
 static_assert(offsetof(Exchange, raw) % 16 == 0 && RAW_BYTES % 16 == 0, "bulk destinations");
+static_assert(sizeof(Exchange) <= 48 * 1024, "static shared memory");
 
 // Bounded waits that gave up in the kernels of this translation unit (each
 // kernel TU has its own counter; see read_wait_timeouts).
@@ -143,6 +149,7 @@ struct FwdTile {
   int64_t in_idx, in_sh;     // element index of (row 0, column c); row stride
   int64_t out_base, out_sh;  // element index of (fine row 0, fine column 2c)
   int64_t out_sw;
+  int64_t oE;                // element index of (fine row 2(s-6), fine column 2c) in step s
   bool col_ok, vec_ok, odd_ok;
   int own_off;               // INB: byte offset of this thread's clamped column in a raw row
   int raw_len;               // INB: bytes copied per raw row
@@ -206,9 +213,8 @@ struct FwdTile {
     return IO::load(in, in_idx + (int64_t)rc * in_sh, in_dtype);
   }
 
-  // Fine row `fr`, columns 2c and 2c+1.
-  __device__ __forceinline__ void store_pair(int fr, float v0, float v1) const {
-    const int64_t base = out_base + (int64_t)fr * out_sh;
+  // Element index `base` (fine row, column 2c) and the next column.
+  __device__ __forceinline__ void store_pair(int64_t base, float v0, float v1) const {
     if (vec_ok) {
       IO::store2(out, base, v0, v1, out_dtype, k.clamp_float);
     } else if (col_ok) {
@@ -217,12 +223,16 @@ struct FwdTile {
     }
   }
 
-  // Input row `r`, columns c-1 .. c+2.
-  __device__ __forceinline__ void row4(int r, float (&v)[4]) const {
-    const float* p = ex.A[r & 7] + t + 1;
+  // Columns c-1 .. c+2 of the row at `p` (column c-1).
+  __device__ __forceinline__ static void row4(const float* p, float (&v)[4]) {
     v[0] = p[0]; v[1] = p[1]; v[2] = p[2]; v[3] = p[3];
   }
-  __device__ __forceinline__ float own(int r) const { return ex.A[r & 7][t + 2]; }
+  // Publishes input row r, column c (and its repeat slot).
+  __device__ __forceinline__ void put_row(int r, float v) const {
+    const int sl = r & 7;
+    ex.A[sl][t + 2] = v;
+    if (sl < 4) ex.A[sl + 8][t + 2] = v;
+  }
 
   // FULL: a step in the middle of the band, where every stage's row is
   // inside the band (7 <= rs <= H + 4) and every stored row inside the
@@ -234,6 +244,7 @@ struct FwdTile {
     const int rs = s - a0;
     if (!FULL && rs > H + 6) return;  // padding step past the band (uniform)
     const float w = k.w;
+    oE += 2 * out_sh;
 
     const int j = rs + HALO_L;  // load number of row s (the sweep starts at a0 - 4)
     float cur = 0.f;
@@ -248,7 +259,7 @@ struct FwdTile {
       // the slot of load j + KAHEAD was last decoded in step s-2
       if (t == 0 && rs >= -HALO_L && rs + KAHEAD <= H + 5) issue_row(j + KAHEAD, s + KAHEAD);
     } else {
-      ex.A[s & 7][t + 2] = cur;
+      put_row(s, cur);
     }
 
     // ---- stage 5: E(s-6, c) and S(s-7, c) from the previous step's stage 4 --
@@ -264,7 +275,7 @@ struct FwdTile {
       const float e = blend4<BMODE>(D[0], D[1], D[2], D[3], C.pE[0], C.pE[1], C.pE[2], C.pE[3],
                                     C.pE[4], C.pE[5], k.beta);
       const int rE = s - 6;  // fine row 2 rE: [A, E]
-      if (FULL || (rE < n && 2 * rE < orows)) store_pair(2 * rE, C.a5c, e);
+      if (FULL || (rE < n && 2 * rE < orows)) store_pair(oE, C.a5c, e);
     }
     if (FULL || rs >= 7) {
       const float4 v = ex.VE[PH ^ 1][t];  // column c-1
@@ -276,15 +287,17 @@ struct FwdTile {
       const float sv = blend4<BMODE>(D[0], D[1], D[2], D[3], p[0], p[1], p[2], p[3], p[4], p[5],
                                      k.beta);
       const int rS = s - 7;  // fine row 2 rS + 1: [S, X]
-      if (FULL || (rS < n && 2 * rS + 1 < orows)) store_pair(2 * rS + 1, sv, C.x6);
+      if (FULL || (rS < n && 2 * rS + 1 < orows)) store_pair(oE - out_sh, sv, C.x6);
     }
 
 
+    // Input rows s-5 .. s-1 sit at consecutive slots from (s-5) & 7.
+    const float* A5 = ex.A[(s - 5) & 7] + t + 1;  // row s-5, column c-1
     // Input rows s-3, s-2, s-1 at columns c-1..c+2 (index u + 1).
     float a1[4], a2[4], a3[4];
-    row4(s - 1, a1);
-    row4(s - 2, a2);
-    row4(s - 3, a3);
+    row4(A5 + 4 * ROW, a1);
+    row4(A5 + 3 * ROW, a2);
+    row4(A5 + 2 * ROW, a3);
 
     // ---- stage 1: diagonal second differences at row s-2, columns c, c+1 --
     // S1(i,j) = A(i-1,j-1) - 2A(i,j) + A(i+1,j+1);  S2 along (1,-1)
@@ -338,7 +351,9 @@ struct FwdTile {
       const float* px = C.px[Q];
       x4 = blend4<BMODE>(D[0], D[1], D[2], D[3], px[0], px[1], px[2], px[3], px[4], px[5],
                          k.beta);
-      ex.X[(s - 4) & 3][t + 2] = x4;
+      const int xs = (s - 4) & 3;
+      ex.X[xs][t + 2] = x4;
+      if (xs == 0) ex.X[4][t + 2] = x4;
     }
 
     // ---- stage 4: phase-2 indicators at row r = s-5 -------------------------
@@ -347,17 +362,18 @@ struct FwdTile {
     // next step as the one centred at A(r), so it starts one row early.
     float a5[4] = {0.f, 0.f, 0.f, 0.f}, a4 = 0.f;
     if (FULL || rs >= 3) {
-      row4(s - 5, a5);
-      a4 = own(s - 4);
+      row4(A5, a5);
+      a4 = A5[ROW + 1];
       C.sVc[PH] = fmaf(-2.f, a4, a5[1] + a3[1]);
       C.qVc[PH] = sq_eps(k.kappa2, C.sVc[PH], k.eps2);
     }
     float DEp[4], DSp[4], pE[6], x6 = 0.f;
     if (FULL || rs >= 4) {
       // phase-1 row r at columns c-2..c+1, and column c at row r-1
-      const float* xp = ex.X[(s - 5) & 3] + t;
+      const float* x6p = ex.X[(s - 6) & 3] + t;  // rows s-6, s-5 at consecutive slots
+      const float* xp = x6p + ROW;
       const float xr0 = xp[0], xr1 = xp[1], xr2 = xp[2], xr3 = xp[3];
-      x6 = ex.X[(s - 6) & 3][t + 2];
+      x6 = x6p[2];
       float* SIE = C.SIE[PH];
       float* SIS = C.SIS[PH];
       float* pS = C.pS[PH];
@@ -422,7 +438,7 @@ struct FwdTile {
       // input row s (slot s & 7 last held row s-8, last read in step s-3);
       // first read in step s+1, so this wait delays no barrier
       await_row(j);
-      ex.A[s & 7][t + 2] = IO::decode(ex.raw[j & (RING - 1)] + own_off, in_dtype);
+      put_row(s, IO::decode(ex.raw[j & (RING - 1)] + own_off, in_dtype));
     }
   }
 
@@ -466,6 +482,7 @@ struct FwdTile {
     float pf = INB ? 0.f : load_row(s_begin);
     float pf2 = INB ? 0.f : load_row(s_begin + 1);
     int s = s_begin;
+    oE = out_base + 2 * (int64_t)(s_begin - 7) * out_sh;  // advanced at the top of each step
     for (; s <= s_end && s - a0 < 7; s += 2) {  // pipeline fill
       step<0, false>(s, pf, pf2, C);
       step<1, false>(s + 1, pf, pf2, C);

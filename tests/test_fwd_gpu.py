@@ -233,3 +233,39 @@ def test_fwd_no_abandoned_waits():
     api.zoom2x_fwd((x * 255).to(torch.uint8))
     torch.cuda.synchronize()
     assert B.weno_wait_timeouts() == 0
+
+
+def test_fwd_weight_forms_at_the_range_limits():
+    """beta = 2 weights are taken as 1/D^2 directly when the input type bounds
+    the data (uint8, FP16) and the eps / h setting keeps every weight in the
+    FP32 range, else in the scale-free form (D_min/D)^2.  Parity on both
+    sides of that choice: FP16 data at the ends of its range, a vanishing
+    eps_h (tiny k_eps or h) and a huge neighbour weight (large h)."""
+    big = scenes.planar(scenes.piecewise_smooth(31, 260, seed=scenes.seed_for(4, 9),
+                                                scale_features=True)).astype(np.float64)
+    big = (big / 255.0 * 2.0 - 1.0) * 65504.0  # FP16 range, both signs
+    big[0, 3, 10:20] = 65504.0
+    big[1, 7, 40:44] = -65504.0
+    x = torch.from_numpy(big.astype(np.float16))
+    for prm in (api.Params(), api.Params(si_scale=1), api.Params(h=1e4)):
+        out = api.zoom2x_fwd(x.to(DEV), prm, out_dtype=torch.float32)
+        torch.cuda.synchronize()
+        ref = parity.oracle_planes(x.double().numpy(), prm)
+        parity.compare(out, ref, "f32", value_range=float(ref.max() - ref.min()))
+    A = scenes.planar(scenes.pixel_art(40, 250, scenes.seed_for(4, 10))) / 255.0
+    for prm in (api.Params(k_eps=1e-30), api.Params(h=1e-6), api.Params(h=1e4),
+                api.Params(h=1e-6, k_eps=1e6)):
+        for in_dt in ("u8", "f16"):
+            out, ref = _run(A, in_dt, "f32", prm)
+            parity.compare(out, ref, "f32")
+
+
+def test_fwd_direct_and_scale_free_weights_agree():
+    """The same FP16 values zoomed from FP16 storage (direct 1/D^2 weights)
+    and from FP32 storage (scale-free weights, the type does not bound the
+    data) agree to a few FP32 rounding steps."""
+    x = torch.rand(3, 77, 300, device=DEV).to(torch.float16)
+    a = api.zoom2x_fwd(x, out_dtype=torch.float32)
+    b = api.zoom2x_fwd(x.float(), out_dtype=torch.float32)
+    torch.cuda.synchronize()
+    assert (a - b).abs().max().item() <= 4e-6
