@@ -272,6 +272,9 @@ int weno_zoom2x_bwd(const weno_image* x, const weno_image* grad_out, const weno_
       reinterpret_cast<uintptr_t>(workspace) % 16 != 0)
     return WENO_EWORKSPACE;
   if ((x->height + 2 * BWD_GHOST + 7) / 8 > 65535) return WENO_ERANGE;
+  // the adjoint kernels index a plane's cells with 32-bit integers
+  if ((x->height + 2 * BWD_GHOST) * (x->width + 2 * BWD_GHOST) + 3 >= (int64_t(1) << 31))
+    return WENO_ERANGE;
   MethodConsts k;
   int bmode;
   if (!fold_consts(p, &k, &bmode)) return WENO_EINVAL;

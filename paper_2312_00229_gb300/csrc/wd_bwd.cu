@@ -16,7 +16,9 @@
 // Every quantity is computed once per cell of a grid extended by BWD_GHOST
 // cells per side (clamp-to-edge) and kept in the workspace; scatters are
 // written as gathers over these arrays (no atomics):
-//   k_xsi      phase-1 indicators (4 directions) of every x point
+//   k_xsi      phase-1 indicators (4 directions) of every x point, and the
+//              clamp-extended copy of the input that the later kernels read
+//              their stencil nodes from (no clamping or 64-bit indexing)
 //   k_xval     phase-1 values X
 //   k_psi      phase-2 indicators of every E and S point
 //   k_padj     p_bar, D_bar of the "+" points that receive an output gradient
@@ -53,7 +55,8 @@ enum Slot {
   S_XB = 2,    // X_bar
   S_ECO = 3,   // 12: E coefficients, index k*3 + t   (phase 1 reuses for x)
   S_SCO = 15,  // 12: S coefficients
-  S_N = 27
+  S_A = 27,    // the input, clamp-extended to the work grid
+  S_N = 28
 };
 static_assert(4 * G_N + S_N == BWD_ARRAYS, "workspace slot count");
 
@@ -86,7 +89,7 @@ struct Ctx {
   int64_t sh, sw;
   float* ws;       // workspace plane
   int NE, ME;
-  int64_t plane_cells;  // NE * ME rounded up to a multiple of 4
+  int64_t plane_cells;  // NE * ME rounded up to a multiple of 4 (< 2^31, checked on the host)
   float w, kap1, kap2, eps1, eps2, beta;
 };
 
@@ -102,8 +105,9 @@ __device__ __forceinline__ bool in_ext(const Ctx& c, int I, int J) {
   return I >= -G && I < c.n + G && J >= -G && J < c.m + G;
 }
 
-__device__ __forceinline__ int64_t cell(const Ctx& c, int I, int J) {
-  return (int64_t)(I + G) * c.ME + (J + G);
+// 32-bit: the cell count of a plane is below 2^31.
+__device__ __forceinline__ int cell(const Ctx& c, int I, int J) {
+  return (I + G) * c.ME + (J + G);
 }
 
 __device__ __forceinline__ float& W(const Ctx& c, int slot, int I, int J) {
@@ -131,9 +135,14 @@ __device__ __forceinline__ float4 f4(const float a[4]) {
   return make_float4(a[0], a[1], a[2], a[3]);
 }
 
+// Stencil node of a point: input samples from the clamp-extended copy (or,
+// with COPY = false, clamped reads of the input itself), x points from the
+// phase-1 values.  Every caller's nodes lie inside the work grid.
+template <bool COPY = true>
 __device__ __forceinline__ float node(const Ctx& c, int type, int k, int t, int a, int b) {
   const int i = a + off_of(type, k, t, 0), j = b + off_of(type, k, t, 1);
-  return lattice_of(type, k) == 0 ? Ahat(c, i, j) : W(c, S_X, i, j);
+  if (lattice_of(type, k) == 1) return W(c, S_X, i, j);
+  return COPY ? W(c, S_A, i, j) : Ahat(c, i, j);
 }
 
 struct Pt {
@@ -143,15 +152,16 @@ struct Pt {
   float s[4];   // second differences
 };
 
+template <bool COPY = true>
 __device__ __forceinline__ Pt eval_pt(const Ctx& c, int type, int a, int b) {
   Pt q;
   const float kap = type == 0 ? c.kap1 : c.kap2;
   const float eps = type == 0 ? c.eps1 : c.eps2;
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    const float n0 = node(c, type, k, 0, a, b);
-    const float n1 = node(c, type, k, 1, a, b);
-    const float n2 = node(c, type, k, 2, a, b);
+    const float n0 = node<COPY>(c, type, k, 0, a, b);
+    const float n1 = node<COPY>(c, type, k, 1, a, b);
+    const float n2 = node<COPY>(c, type, k, 2, a, b);
     const float g = n1 - n0;
     const float s = fmaf(-2.f, n1, n0 + n2);
     const float ks = kap * s;
@@ -239,11 +249,12 @@ __global__ void k_xsi(BwdArgs a, MethodConsts k) {
   if (!setup(a, k, c, I, J)) return;
   float si[4] = {0.f, 0.f, 0.f, 0.f};
   if (in_core(c, I, J)) {
-    const Pt q = eval_pt(c, 0, I, J);
+    const Pt q = eval_pt<false>(c, 0, I, J);
 #pragma unroll
     for (int d = 0; d < 4; ++d) si[d] = q.si[d];
   }
   V(c, G_XSI, I, J) = f4(si);
+  W(c, S_A, I, J) = Ahat(c, I, J);
 }
 
 template <int BMODE>
