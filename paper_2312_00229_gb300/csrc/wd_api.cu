@@ -156,6 +156,25 @@ bool direct_b2_ok(const weno_params& p, int in_t) {
   return 8.0 * a_max <= 1e37 && 16.0 * v * a_max <= 1e37;
 }
 
+// The same choice for the 1-D WENO weights of the tensor resampling: with
+// indicators e = g^2 + 13/12 s^2 + eps, alpha_0 : alpha_1 = C_0 eR^2 : C_1 eL^2
+// as written needs eps^2 normal and (e_max)^2 times the largest |s| finite.
+// The nodes are inputs or first-pass values, quadratic interpolants on
+// [0, 1] of inputs (|p| <= 1.25 max|node|).
+bool resample_direct_ok(int in_t, double eps) {
+  double v0;
+  if (in_t == WENO_U8) {
+    v0 = 1.0;
+  } else if (in_t == WENO_F16) {
+    v0 = 65504.0;
+  } else {
+    return false;
+  }
+  const double v = 1.25 * v0 * (1.0 + 1e-3);
+  const double e_hi = 4.0 * v * v + 13.0 / 12.0 * 16.0 * v * v + eps;
+  return eps >= 1e-18 && e_hi <= 1e18 && e_hi * e_hi * 4.0 * v <= 1e37;
+}
+
 int check_pair(const weno_image* in, int in_t, const weno_image* out, int out_t,
                const weno_params& p, int64_t* orows, int64_t* ocols) {
   if (!image_ok(in) || !image_ok(out)) return WENO_EINVAL;
@@ -362,6 +381,7 @@ int weno_resample(const weno_image* in, weno_dtype in_t, const weno_image* out,
   a.win_rows = 0;
   // a floor of 1e-30 keeps the larger indicator a normal FP32 number
   const float eps = std::max(float(double(p.k_eps) * double(p.h) * double(p.h)), 1e-30f);
+  if (bmode == B2 && resample_direct_ok(in_t, eps)) bmode = B2R;
   cudaError_t e = launch_resample(a, eps, p.beta, bmode, static_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? WENO_OK : WENO_ECUDA;
 }

@@ -23,17 +23,26 @@ namespace wdweno {
 
 namespace {
 
+// With the position's constants given: C0 = (2 - t)/3 and h = (t^2 - t)/2.
 template <int BMODE>
-__device__ __forceinline__ float weno1d(float v0, float v1, float v2, float v3, float t,
-                                        float eps, float beta) {
+__device__ __forceinline__ float weno1d_at(float v0, float v1, float v2, float v3, float t,
+                                           float C0, float h, float eps, float beta) {
   const float g = v2 - v1;
   const float sL = fmaf(-2.f, v1, v0 + v2);
   const float sR = fmaf(-2.f, v2, v1 + v3);
-  const float C0 = (2.f - t) * (1.f / 3.f);
   const float C1 = 1.f - C0;
   float a0, a1;
   if (BMODE == B0) {
     a0 = C0; a1 = C1;
+  } else if (BMODE == B2R) {
+    // alpha_0 : alpha_1 = C_0 eR^2 : C_1 eL^2 as written; the host picks
+    // this form only where the storage type bounds the data so that every
+    // square, their sum and the numerator below are normal FP32 numbers
+    const float k2 = 13.f / 12.f;
+    const float eL = fmaf(g, g, fmaf(k2 * sL, sL, eps));
+    const float eR = fmaf(g, g, fmaf(k2 * sR, sR, eps));
+    a0 = C0 * (eR * eR);
+    a1 = C1 * (eL * eL);
   } else {
     // alpha_0 : alpha_1 = C_0 eR^beta : C_1 eL^beta with both indicators
     // divided by the larger one, so no power over- or underflows.  eps is
@@ -50,21 +59,41 @@ __device__ __forceinline__ float weno1d(float v0, float v1, float v2, float v3, 
       a1 = C1 * ex2_approx(beta * lg2_approx(rL));
     }
   }
-  // a0 + a1 >= 1/3: one ratio is 1 and both C_s are at least 1/3
+  // a0 + a1 >= 1/3 in the scaled forms: one ratio is 1 and both C_s are at
+  // least 1/3
   const float mix = fmaf(a0, sL, a1 * sR) * rcp_approx(a0 + a1);
-  return fmaf(0.5f * fmaf(t, t, -t), mix, fmaf(g, t, v1));
+  return fmaf(h, mix, fmaf(g, t, v1));
+}
+
+template <int BMODE>
+__device__ __forceinline__ float weno1d(float v0, float v1, float v2, float v3, float t,
+                                        float eps, float beta) {
+  return weno1d_at<BMODE>(v0, v1, v2, v3, t, (2.f - t) * (1.f / 3.f), 0.5f * fmaf(t, t, -t),
+                          eps, beta);
 }
 
 // Cell index and offset of output index j on the endpoint-aligned grid of
-// n_out points over 0..n-1, in exact integer arithmetic.
-__device__ __forceinline__ void grid_pos(int64_t j, int64_t n, int64_t n_out, int64_t& i,
-                                         float& t) {
+// n_out points over 0..n-1: i = floor(j (n-1) / (n_out-1)) exactly (by
+// multiply-high when the numerator fits 32 bits), t = remainder / (n_out-1).
+__device__ __forceinline__ void grid_pos(int64_t j, int64_t n, int64_t n_out, const AxisDiv& d,
+                                         int64_t& i, float& t) {
   if (n <= 1 || n_out <= 1) { i = 0; t = 0.f; return; }
-  const int64_t num = j * (n - 1), den = n_out - 1;
-  i = num / den;
-  int64_t rem = num - i * den;
-  if (i > n - 2) { i = n - 2; rem = den; }  // last sample: t = 1 on the last cell
-  t = (float)((double)rem / (double)den);
+  const int64_t den = n_out - 1;
+  int64_t q, rem;
+  if (d.fast) {
+    const uint32_t num = (uint32_t)j * (uint32_t)(n - 1);
+    const uint32_t t1 = __umulhi(d.mag, num);
+    const uint32_t qq = (t1 + ((num - t1) >> d.sh1)) >> d.sh2;
+    q = qq;
+    rem = (int64_t)(num - qq * (uint32_t)den);
+  } else {
+    const int64_t num = j * (n - 1);
+    q = num / den;
+    rem = num - q * den;
+  }
+  if (q > n - 2) { q = n - 2; rem = den; }  // last sample: t = 1 on the last cell
+  i = q;
+  t = rem == den ? 1.f : (float)rem * d.inv;
 }
 
 template <int BMODE>
@@ -75,8 +104,8 @@ __global__ void __launch_bounds__(256) resample_kernel(ResampleArgs a, float eps
   const int64_t plane = blockIdx.z;
   int64_t i, j;
   float ty, tx;
-  grid_pos(r, a.n, a.n_out, i, ty);
-  grid_pos(c, a.m, a.m_out, j, tx);
+  grid_pos(r, a.n, a.n_out, a.div_y, i, ty);
+  grid_pos(c, a.m, a.m_out, a.div_x, j, tx);
   const int64_t base = plane * a.in_sc;
   float z[4];
 #pragma unroll
@@ -159,24 +188,24 @@ __global__ void __launch_bounds__(RS_THREADS) resample_tiled_kernel(ResampleArgs
   const int nr = (int)(a.n_out - r0 < RS_TR ? a.n_out - r0 : RS_TR);
   int64_t jf, jl, i_first, i_last;
   float tdummy;
-  grid_pos(c0, a.m, a.m_out, jf, tdummy);
-  grid_pos(c0 + nc - 1, a.m, a.m_out, jl, tdummy);
-  grid_pos(r0, a.n, a.n_out, i_first, tdummy);
-  grid_pos(r0 + nr - 1, a.n, a.n_out, i_last, tdummy);
+  grid_pos(c0, a.m, a.m_out, a.div_x, jf, tdummy);
+  grid_pos(c0 + nc - 1, a.m, a.m_out, a.div_x, jl, tdummy);
+  grid_pos(r0, a.n, a.n_out, a.div_y, i_first, tdummy);
+  grid_pos(r0 + nr - 1, a.n, a.n_out, a.div_y, i_last, tdummy);
   const int64_t kfirst = jf - 1, ifirst = i_first - 1;
   const int wc = (int)(jl + 2 - kfirst + 1);       // <= RS_WC (host checks the x scale)
   const int wr = (int)(i_last + 2 - ifirst + 1);   // <= a.win_rows (host sizes it)
   if (tid < nc) {
     int64_t j;
     float t;
-    grid_pos(c0 + tid, a.m, a.m_out, j, t);
+    grid_pos(c0 + tid, a.m, a.m_out, a.div_x, j, t);
     col_j[tid] = (int)(j - 1 - kfirst);
     col_t[tid] = t;
   }
   if (tid >= RS_TC && tid - RS_TC < nr) {
     int64_t i;
     float t;
-    grid_pos(r0 + tid - RS_TC, a.n, a.n_out, i, t);
+    grid_pos(r0 + tid - RS_TC, a.n, a.n_out, a.div_y, i, t);
     row_i[tid - RS_TC] = (int)(i - 1 - ifirst);
     row_t[tid - RS_TC] = t;
   }
@@ -195,32 +224,45 @@ __global__ void __launch_bounds__(RS_THREADS) resample_tiled_kernel(ResampleArgs
   __syncthreads();
   // pass 1: column interpolants
   for (int r = warp; r < nr; r += RS_THREADS / 32) {
-    const int ib = row_i[r];
-    const float ty = row_t[r];
-    for (int k = lane; k < wc; k += 32)
-      z[r][k] = a.n > 1 ? weno1d<BMODE>(win[ib][k], win[ib + 1][k], win[ib + 2][k], win[ib + 3][k],
-                                        ty, eps, beta)
-                        : win[ib + 1][k];
+    const float* w0 = win[row_i[r]];
+    if (a.n > 1) {
+      const float ty = row_t[r];
+      const float C0 = (2.f - ty) * (1.f / 3.f), h = 0.5f * fmaf(ty, ty, -ty);
+      for (int k = lane; k < wc; k += 32)
+        z[r][k] = weno1d_at<BMODE>(w0[k], w0[k + RS_WC], w0[k + 2 * RS_WC], w0[k + 3 * RS_WC],
+                                   ty, C0, h, eps, beta);
+    } else {
+      for (int k = lane; k < wc; k += 32) z[r][k] = w0[k + RS_WC];
+    }
   }
   __syncthreads();
-  // pass 2: four consecutive outputs per thread
+  // pass 2: four consecutive outputs per thread; the column positions and
+  // their constants are the same for every row of the tile
   const int c = lane * 4;
   if (c >= nc) return;
   const int cn = nc - c < 4 ? nc - c : 4;
-  for (int r = warp; r < nr; r += RS_THREADS / 32) {
+  int kq[4];
+  float tq[4], cq[4], hq[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int cc = c + (q < cn ? q : 0);  // columns past the tile repeat the first (not stored)
+    kq[q] = col_j[cc];
+    tq[q] = col_t[cc];
+    cq[q] = (2.f - tq[q]) * (1.f / 3.f);
+    hq[q] = 0.5f * fmaf(tq[q], tq[q], -tq[q]);
+  }
+  const bool interp_x = a.m > 1;
+  int64_t o = plane * a.out_sc + (r0 + warp) * a.out_sh + (c0 + c) * a.out_sw;
+  const int64_t o_step = (RS_THREADS / 32) * a.out_sh;
+  for (int r = warp; r < nr; r += RS_THREADS / 32, o += o_step) {
     float u[4];
+    const float* zr = z[r];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      if (q < cn) {
-        const int k = col_j[c + q];
-        u[q] = a.m > 1 ? weno1d<BMODE>(z[r][k], z[r][k + 1], z[r][k + 2], z[r][k + 3],
-                                       col_t[c + q], eps, beta)
-                       : z[r][k + 1];
-      } else {
-        u[q] = 0.f;
-      }
+      const float* zk = zr + kq[q];
+      u[q] = interp_x ? weno1d_at<BMODE>(zk[0], zk[1], zk[2], zk[3], tq[q], cq[q], hq[q], eps, beta)
+                      : zk[1];
     }
-    const int64_t o = plane * a.out_sc + (r0 + r) * a.out_sh + (c0 + c) * a.out_sw;
     if (a.out_vec4 && cn == 4) {
       rs_store4<TOut>(a.out, o, u, a.out_dtype, a.clamp_float);
     } else {
@@ -250,6 +292,7 @@ cudaError_t launch_tiled_beta(const ResampleArgs& a, float eps, float beta, int 
                               cudaStream_t stream) {
   switch (bmode) {
     case B2: return launch_tiled<B2, TIn, TOut>(a, eps, beta, stream);
+    case B2R: return launch_tiled<B2R, TIn, TOut>(a, eps, beta, stream);
     case B0: return launch_tiled<B0, TIn, TOut>(a, eps, beta, stream);
     default: return launch_tiled<BGEN, TIn, TOut>(a, eps, beta, stream);
   }
@@ -257,9 +300,29 @@ cudaError_t launch_tiled_beta(const ResampleArgs& a, float eps, float beta, int 
 
 }  // namespace
 
+static AxisDiv axis_div(int64_t n, int64_t n_out) {
+  AxisDiv d{1u, 0, 0, 0, 0.f};
+  if (n <= 1 || n_out <= 1) return d;
+  const uint64_t den = (uint64_t)(n_out - 1);
+  d.inv = (float)(1.0 / (double)den);
+  // the largest numerator is (n_out - 1)(n - 1)
+  if (den >= (1ull << 32) || (uint64_t)(n - 1) >= (1ull << 32) ||
+      den * (uint64_t)(n - 1) >= (1ull << 32))
+    return d;
+  int l = 0;
+  while ((1ull << l) < den) ++l;
+  d.mag = (uint32_t)(((1ull << 32) * ((1ull << l) - den)) / den + 1);
+  d.sh1 = l < 1 ? l : 1;
+  d.sh2 = l > 1 ? l - 1 : 0;
+  d.fast = 1;
+  return d;
+}
+
 cudaError_t launch_resample(const ResampleArgs& a_in, float eps, float beta, int bmode,
                             cudaStream_t stream) {
   ResampleArgs a = a_in;
+  a.div_y = axis_div(a.n, a.n_out);
+  a.div_x = axis_div(a.m, a.m_out);
   // the tiled form reads at most RS_WC window columns and sizes its window
   // rows from the y ratio: spacing ratios (n - 1)/(n_out - 1) <= 2 per axis
   const bool tiled = (a.m_out == 1 || 2 * (a.m_out - 1) >= (a.m - 1)) &&
@@ -281,6 +344,7 @@ cudaError_t launch_resample(const ResampleArgs& a_in, float eps, float beta, int
                   (unsigned)a.planes);
   switch (bmode) {
     case B2: resample_kernel<B2><<<grid, block, 0, stream>>>(a, eps, beta); break;
+    case B2R: resample_kernel<B2R><<<grid, block, 0, stream>>>(a, eps, beta); break;
     case B0: resample_kernel<B0><<<grid, block, 0, stream>>>(a, eps, beta); break;
     default: resample_kernel<BGEN><<<grid, block, 0, stream>>>(a, eps, beta); break;
   }

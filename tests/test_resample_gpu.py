@@ -140,3 +140,44 @@ def test_resample_rejects_bad_arguments():
         api.resample(x, 0, 5)
     with pytest.raises(Exception):
         api.resample(x, 5, 5, out=torch.zeros(2, 5, 5, device=DEV))  # channel mismatch
+
+
+def test_resample_weight_forms_at_the_range_limits():
+    """beta = 2 weights as C_0 eR^2 : C_1 eL^2 directly for uint8 and FP16
+    data (range-bounded), else scaled by the larger indicator: parity on both
+    sides, with FP16 data at the ends of its range and vanishing eps."""
+    big = scenes.planar(scenes.piecewise_smooth(41, 57, seed=scenes.seed_for(6, 4),
+                                                scale_features=True)).astype(np.float64)
+    big = (big / 255.0 * 2.0 - 1.0) * 65504.0
+    big[0, 5, 3:9] = 65504.0
+    big[2, 9, 20:23] = -65504.0
+    x = torch.from_numpy(big.astype(np.float16))
+    out = api.resample(x.to(DEV), 100, 131, out_dtype=torch.float32)
+    torch.cuda.synchronize()
+    ref = oracle.tensor_resample(x.double().numpy(), 100, 131)
+    parity.compare(out, ref, "f32", value_range=float(ref.max() - ref.min()))
+    img = scenes.pixel_art(30, 44, seed=scenes.seed_for(6, 5))
+    A = scenes.planar(img).astype(np.float64) / 255.0
+    for prm in (api.Params(k_eps=1e-30), api.Params(h=1e-6), api.Params(h=1e-6, k_eps=1e6)):
+        for in_dt in ("u8", "f16"):
+            out, ref = _resample(A, 90, 131, in_dt, "f32", params=prm)
+            parity.compare(out, ref, "f32")
+
+
+def test_resample_direct_and_scaled_weights_agree():
+    """FP16 storage (direct weights) and FP32 storage of the same values
+    (scaled weights) agree to a few FP32 rounding steps."""
+    x = torch.rand(3, 70, 90, device=DEV).to(torch.float16)
+    a = api.resample(x, 209, 270, out_dtype=torch.float32)
+    b = api.resample(x.float(), 209, 270, out_dtype=torch.float32)
+    torch.cuda.synchronize()
+    assert (a - b).abs().max().item() <= 4e-6
+
+
+def test_resample_positions_past_32_bits():
+    """An axis whose position numerators j (m - 1) pass 2^32 (70001 columns
+    to 70001: 4.9e9) takes the 64-bit division; the rows take the 32-bit
+    multiply-high one.  Both against the oracle."""
+    A = RNG.random((1, 2, 70001))
+    out, ref = _resample(A, 5, 70001)
+    parity.compare(out, ref, "f32")
