@@ -132,7 +132,7 @@ size_t weno_zoom2x_batched_workspace_bytes(int count);
  *                 the call can be captured into a CUDA graph and replayed)
  *   workspace   : device buffer of >= weno_zoom2x_batched_workspace_bytes
  *                 bytes; contents need no initialisation and are scratch
- *   rows_per_tile, tile_width : tile shape (0 = library default: 64-row
+ *   rows_per_tile, tile_width : tile shape (0 = library default: 128-row
  *                 bands, 247-column strips); the autotuner chooses the band
  *                 height per size class
  * Shapes follow weno_zoom2x_fwd per image; descriptors are read on the

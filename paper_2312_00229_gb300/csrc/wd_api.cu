@@ -18,6 +18,10 @@ using namespace wdweno;
 namespace {
 
 constexpr int64_t kDefaultRowsPerBand = 64;
+// Persistent batched launches: 128-row bands measured best on 256 FP16 images
+// of sides 64..1024 (77.2 Gpix/s at 64 rows, 78.7 at 128, 76.7 at 192); the
+// queue still holds some 10,000 tiles for 304 CTA slots.
+constexpr int64_t kBatchedRowsPerBand = 128;
 constexpr int kFwdCtasPerSm = 2;  // 256 threads x 128 registers
 
 int sm_count() {
@@ -344,7 +348,7 @@ int weno_zoom2x_batched(int count, const weno_image* d_in, weno_dtype in_t,
   a.in_dtype = in_t;
   a.out_dtype = out_t;
   a.out_mode = p.out_mode;
-  a.rows_per_band = rows_per_tile > 0 ? rows_per_tile : kDefaultRowsPerBand;
+  a.rows_per_band = rows_per_tile > 0 ? rows_per_tile : kBatchedRowsPerBand;
   a.workspace = workspace;
   cudaError_t e = launch_zoom2x_batched(a, k, bmode, static_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? WENO_OK : WENO_ECUDA;
