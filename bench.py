@@ -66,12 +66,15 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--skip-extras", action="store_true",
                     help="headline only (no fwd+bwd / batched / sweep / cascade)")
-    ap.add_argument("--case", choices=["headline", "resample3x", "fwdbwd"], default="headline",
+    ap.add_argument("--case", choices=["headline", "resample3x", "fwdbwd", "batched"],
+                    default="headline",
                     help="run one secondary workload alone (for profiling) instead of the "
                          "headline line: resample3x = 1920x1080x3 uint8 -> 5760x3240 tensor "
-                         "WENO; fwdbwd = one autograd step on Bx3x512x512 FP32")
-    ap.add_argument("--batch", type=int, default=32,
-                    help="images per autograd step of --case fwdbwd (the workload has 32)")
+                         "WENO; fwdbwd = one autograd step on Bx3x512x512 FP32; batched = "
+                         "one persistent launch over B uneven FP16 RGB images")
+    ap.add_argument("--batch", type=int, default=None,
+                    help="images per step of --case fwdbwd (default 32, the workload) or "
+                         "--case batched (default 256, the workload)")
     return ap.parse_args()
 
 
@@ -599,7 +602,15 @@ def run_case(args):
         o = torch.empty(3, 3240, 5760, dtype=torch.uint8, device=dev)
         step = lambda: api.resample(hd, 3240, 5760, out=o)
         work = "1920x1080x3 uint8 -> 5760x3240x3 uint8, tensor WENO"
+    elif args.case == "batched":
+        count = args.batch or 256
+        xs = [torch.from_numpy(scenes.planar(im)).to(dev).float().div(255).half()
+              for im in scenes.uneven_batch(count)]
+        plan = api.BatchedPlan(xs)
+        step = plan.run
+        work = f"{count} uneven RGB FP16 images (sides 64..1024), one persistent launch"
     else:
+        args.batch = args.batch or 32
         xb = np.stack([scenes.planar(scenes.piecewise_smooth(512, 512, scenes.seed_for(5, i),
                                                              scale_features=True))
                        for i in range(args.batch)]).astype(np.float32) / 255.0
