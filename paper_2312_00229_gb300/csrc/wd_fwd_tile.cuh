@@ -36,10 +36,11 @@
 // One barrier (B1) opens each step: every shared value a step reads was
 // written in an earlier step, in a slot no thread writes in the same step.
 //
-// Input path.  When the input rows are 16-byte aligned (FwdArgs::in_bulk),
-// thread 0 requests each input row segment of the strip (with its halo)
-// KAHEAD steps ahead as one asynchronous bulk copy into a ring of RING raw
-// rows in shared memory, completing on the slot's mbarrier.  At the end of
+// Input path.  For 1- and 2-byte storage with unit column stride
+// (FwdArgs::in_bulk), thread 0 requests each input row segment of the strip
+// (with its halo; the 16-byte blocks that cover it) KAHEAD steps ahead as one
+// asynchronous bulk copy into a ring of RING raw rows in shared memory,
+// completing on the slot's mbarrier.  At the end of
 // step s every thread waits for row s and decodes its own (clamped) column of
 // it into the float ring (first read in step s+1).  The sweep's barriers do
 // not wait for these copies, unlike register loads issued before them, so the
@@ -62,7 +63,7 @@ constexpr int ROW = THREADS + 4;     // floats per staged row (2 pad each side)
 constexpr int RING = 8;              // raw input rows in flight or in use
 constexpr int KAHEAD = 6;            // rows requested ahead of the sweep (< RING)
 // Raw bytes of one strip row: 256 columns of 1- or 2-byte storage (the only
-// sizes taken by bulk copy) plus up to 16 bytes of alignment slack at each end.
+// sizes taken by bulk copy) widened to 16-byte blocks (at most 528 bytes).
 constexpr int RAW_BYTES = THREADS * 2 + 32;
 // Bound on one wait for an input row (nanoseconds of global time).
 constexpr unsigned long long WAIT_LIMIT_NS = 1000000000ull;
@@ -82,6 +83,7 @@ struct __align__(16) Exchange {
   // --- everything above is zeroed at the start of a tile ---
   unsigned char raw[RING][RAW_BYTES];  // bulk-copied input rows, slot = load index % RING
   uint64_t mbar[RING];                 // completion barrier of each slot
+  int mis[RING];                       // byte offset of the window's first column in the slot
 };
 static_assert(offsetof(Exchange, raw) % 16 == 0 && RAW_BYTES % 16 == 0, "bulk destinations");
 static_assert(sizeof(Exchange) <= 48 * 1024, "static shared memory");
@@ -134,7 +136,13 @@ struct Carry {
   float DEp[4], DSp[4], pE[6], a5c, x6;
 };
 
-template <int BMODE, class IO, bool INB>
+// INB: input path.  IN_REG = register loads two rows ahead; IN_BULK_ALIGNED
+// = bulk copies of rows whose starts are 16-byte aligned (one window offset
+// and length for every row); IN_BULK_ANY = bulk copies of rows that start
+// anywhere (per-row offset, published in Exchange::mis).
+enum InputPath { IN_REG = 0, IN_BULK_ALIGNED = 1, IN_BULK_ANY = 2 };
+
+template <int BMODE, class IO, int INB>
 struct FwdTile {
   // Arguments are held by value so that they stay in registers across the
   // barriers (a reference would be re-read from memory after each one).
@@ -151,8 +159,12 @@ struct FwdTile {
   int64_t out_sw;
   int64_t oE;                // element index of (fine row 2(s-6), fine column 2c) in step s
   bool col_ok, vec_ok, odd_ok;
-  int own_off;               // INB: byte offset of this thread's clamped column in a raw row
-  int raw_len;               // INB: bytes copied per raw row
+  // IN_BULK_ALIGNED: own_rel = offset of this thread's column in a raw slot,
+  //   span = bytes copied per row (the same window for every row);
+  // IN_BULK_ANY: own_rel = bytes from the window's first column to this
+  //   thread's, span = bytes of the window's columns in a row.
+  int own_rel;
+  int span;
 
   __device__ __forceinline__ FwdTile(const FwdArgs& a, const MethodConsts& k_, Exchange& ex_,
                                      int64_t bx, int64_t by, int64_t plane)
@@ -175,31 +187,53 @@ struct FwdTile {
     out_sw = a.out_sw;
     out_sh = a.out_sh;
     out_base = plane * a.out_sc + 2 * c * a.out_sw;
-    if (INB) {
-      // window = the strip's columns b0-4 .. b0+251 inside the image, widened
-      // to 16-byte boundaries (the row length is a multiple of 16 bytes)
+    if constexpr (INB != IN_REG) {
+      // window = the strip's columns b0-4 .. b0+251 inside the image
       const int64_t esz = IO::in_size(in_dtype);
-      const int64_t lo = ((b0 - HALO_L > 0 ? b0 - HALO_L : 0) * esz) & ~int64_t(15);
+      const int64_t lo_c = b0 - HALO_L > 0 ? b0 - HALO_L : 0;
       int64_t hi_c = b0 - HALO_L + THREADS;
       if (hi_c > a.m) hi_c = a.m;
-      const int64_t hi = (hi_c * esz + 15) & ~int64_t(15);
-      raw_len = (int)(hi - lo);
-      own_off = (int)(clamp64(c, 0, a.m - 1) * esz - lo);
+      if constexpr (INB == IN_BULK_ALIGNED) {
+        // row starts are 16-byte aligned: the window widened to 16-byte blocks
+        const int64_t lo = (lo_c * esz) & ~int64_t(15);
+        const int64_t hi = (hi_c * esz + 15) & ~int64_t(15);
+        span = (int)(hi - lo);
+        own_rel = (int)(clamp64(c, 0, a.m - 1) * esz - lo);
+      } else {
+        span = (int)((hi_c - lo_c) * esz);
+        own_rel = (int)((clamp64(c, 0, a.m - 1) - lo_c) * esz);
+      }
     } else {
-      raw_len = 0;
-      own_off = 0;
+      span = 0;
+      own_rel = 0;
     }
   }
 
   // Thread 0: requests input row r (clamped) as load number j into its slot.
+  // The copy covers the 16-byte blocks that hold the window's columns, so a
+  // row may start anywhere; a 16-byte block never straddles a page, so the
+  // bytes before and after the window that come along are mapped memory,
+  // and no thread decodes them.
   __device__ __forceinline__ void issue_row(int j, int r) const {
     const int rc = r < 0 ? 0 : (r > n - 1 ? n - 1 : r);
-    // thread 0's in_idx is the first window column of row 0; own_off its offset
-    const unsigned char* src = static_cast<const unsigned char*>(in) +
-                               (in_idx + (int64_t)rc * in_sh) * IO::in_size(in_dtype) - own_off;
-    uint64_t* bar = &ex.mbar[j & (RING - 1)];
-    mbar_arrive_expect_tx(bar, (uint32_t)raw_len);
-    bulk_g2s(ex.raw[j & (RING - 1)], src, (uint32_t)raw_len, bar);
+    // thread 0's in_idx is the window's first column of row 0
+    const unsigned char* first = static_cast<const unsigned char*>(in) +
+                                 (in_idx + (int64_t)rc * in_sh) * IO::in_size(in_dtype);
+    const int slot = j & (RING - 1);
+    const unsigned char* src;
+    uint32_t len;
+    if constexpr (INB == IN_BULK_ALIGNED) {
+      src = first - own_rel;  // thread 0's offset in the slot
+      len = (uint32_t)span;
+    } else {
+      const int mis = (int)(reinterpret_cast<uintptr_t>(first) & 15);
+      src = first - mis;
+      len = (uint32_t)((mis + span + 15) & ~15);
+      ex.mis[slot] = mis;  // read KAHEAD steps later, after as many barriers
+    }
+    uint64_t* bar = &ex.mbar[slot];
+    mbar_arrive_expect_tx(bar, len);
+    bulk_g2s(ex.raw[slot], src, len, bar);
   }
 
   // Waits (bounded) for load number j.
@@ -248,14 +282,19 @@ struct FwdTile {
 
     const int j = rs + HALO_L;  // load number of row s (the sweep starts at a0 - 4)
     float cur = 0.f;
-    if (!INB) {
+    if constexpr (INB == IN_REG) {
       cur = pf;               // input row s, loaded in step s-2
       pf = pf2;
       pf2 = load_row(s + 2);  // prefetch two rows ahead
     }
 
     __syncthreads();  // B1: rows published in step s-1 are visible
-    if (INB) {
+    // IN_BULK_ANY: byte offset of this thread's column in the raw slot of row
+    // s; thread 0 wrote the slot's offset when it requested the row, KAHEAD
+    // steps ago, so the barriers since then make it visible without the wait
+    int any_off = 0;
+    if constexpr (INB == IN_BULK_ANY) any_off = ex.mis[j & (RING - 1)] + own_rel;
+    if constexpr (INB != IN_REG) {
       // the slot of load j + KAHEAD was last decoded in step s-2
       if (t == 0 && rs >= -HALO_L && rs + KAHEAD <= H + 5) issue_row(j + KAHEAD, s + KAHEAD);
     } else {
@@ -434,11 +473,12 @@ struct FwdTile {
       C.x6 = x6;
     }
 
-    if (INB && (FULL || (rs >= -HALO_L && rs <= H + 5))) {
+    if (INB != IN_REG && (FULL || (rs >= -HALO_L && rs <= H + 5))) {
       // input row s (slot s & 7 last held row s-8, last read in step s-3);
       // first read in step s+1, so this wait delays no barrier
       await_row(j);
-      put_row(s, IO::decode(ex.raw[j & (RING - 1)] + own_off, in_dtype));
+      put_row(s, IO::decode(ex.raw[j & (RING - 1)] + (INB == IN_BULK_ANY ? any_off : own_rel),
+                            in_dtype));
     }
   }
 
@@ -458,7 +498,7 @@ struct FwdTile {
     const int s_last = a0 + H + 5;   // last input row of the band's sweep
     const int s_end = s_last + 1;    // inclusive: one more step finishes stage 5
     const int loads = s_last - s_first + 1;
-    if (INB && t == 0) {
+    if (INB != IN_REG && t == 0) {
       for (int i = 0; i < RING; ++i) mbar_init(&ex.mbar[i], 1);
       fence_mbar_init();
       for (int j = 0; j < KAHEAD && j < loads; ++j) issue_row(j, s_first + j);
@@ -479,8 +519,8 @@ struct FwdTile {
 #pragma unroll
     for (int d = 0; d < 6; ++d) C.pE[d] = 0.f;
     C.a5c = C.x6 = 0.f;
-    float pf = INB ? 0.f : load_row(s_begin);
-    float pf2 = INB ? 0.f : load_row(s_begin + 1);
+    float pf = INB != IN_REG ? 0.f : load_row(s_begin);
+    float pf2 = INB != IN_REG ? 0.f : load_row(s_begin + 1);
     int s = s_begin;
     oE = out_base + 2 * (int64_t)(s_begin - 7) * out_sh;  // advanced at the top of each step
     for (; s <= s_end && s - a0 < 7; s += 2) {  // pipeline fill
@@ -496,7 +536,7 @@ struct FwdTile {
       step<0, false>(s, pf, pf2, C);
       step<1, false>(s + 1, pf, pf2, C);
     }
-    if (INB) {
+    if (INB != IN_REG) {
       __syncthreads();  // every thread has decoded its last row
       if (t == 0) {
         // Every issued row was waited for; after an abandoned wait a copy
@@ -558,7 +598,7 @@ struct DynIO {
   }
 };
 
-template <int BMODE, class IO, bool INB>
+template <int BMODE, class IO, int INB>
 __device__ __forceinline__ void zoom2x_fwd_tile(const FwdArgs& a, const MethodConsts& k,
                                                 Exchange& ex, int64_t bx, int64_t by,
                                                 int64_t plane) {

@@ -103,3 +103,24 @@ def test_batched_uneven_scenes_against_oracle():
         if hh > 0 and ww > 0:
             parity.compare(outs[k][:, : 2 * hh, : 2 * ww].cpu(), ref[:, : 2 * hh, : 2 * ww],
                            "f16")
+
+
+@pytest.mark.parametrize("dtype", [torch.uint8, torch.bfloat16])
+def test_batched_mixed_input_paths(dtype):
+    """One call whose images take both input paths: unit column stride (bulk
+    row copies, including rows at odd byte offsets) and column stride 2
+    (register loads); each equals the single-image kernel bit for bit."""
+    base = _images(dtype, [(37, 251), (64, 97), (5, 513), (130, 256), (1, 3)], seed=11)
+    imgs = []
+    for i, x in enumerate(base):
+        if i % 2:
+            wide = torch.zeros(x.shape[:-1] + (2 * x.shape[-1],), device=DEV, dtype=dtype)
+            wide[..., ::2] = x
+            imgs.append(wide[..., ::2])
+        else:
+            imgs.append(x[:, :, 1:] if x.shape[-1] > 1 else x)  # rows start off 16-byte blocks
+    outs = api.zoom2x_batched(imgs)
+    singles = [api.zoom2x_fwd(x) for x in imgs]
+    torch.cuda.synchronize()
+    for o, s in zip(outs, singles):
+        assert torch.equal(o, s)

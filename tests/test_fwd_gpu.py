@@ -184,8 +184,9 @@ def test_fwd_large_planes_64bit_offsets():
     torch.cuda.empty_cache()
 
 
-# Rows whose byte length, base and strides are multiples of 16 take the
-# asynchronous bulk-copy input path; the others load rows into registers.
+# 1- and 2-byte storage with unit column stride takes the asynchronous
+# bulk-copy input path (whatever the row alignment); FP32 and strided
+# columns load rows into registers.  These widths keep rows 16-byte aligned.
 ALIGNED = [(1, 16), (5, 32), (37, 496), (70, 512), (9, 1024), (130, 256)]
 
 
@@ -207,21 +208,46 @@ def test_fwd_aligned_storage_pairs(in_dt, out_dt):
     parity.compare(out, ref, out_dt)
 
 
+def _register_path_copy(xs):
+    """The same values with column stride 2: rows load through registers."""
+    wide = torch.zeros(xs.shape[:-1] + (2 * xs.shape[-1],), device=DEV, dtype=xs.dtype)
+    wide[..., ::2] = xs
+    return wide[..., ::2]
+
+
 def test_fwd_bulk_and_register_paths_agree_bitwise():
-    """The same values through both input paths (a contiguous image whose
-    rows are bulk-copied, and a copy with padded rows loaded through
-    registers) give bit-identical outputs for every band height."""
-    x = torch.rand(2, 203, 512, device=DEV)
+    """The same values through both input paths (unit column stride: rows
+    bulk-copied; column stride 2: rows loaded through registers) give
+    bit-identical outputs for every band height, for 16-byte aligned rows
+    (width 512) and for rows at every alignment (width 513, padded rows)."""
+    x = torch.rand(2, 203, 513, device=DEV)
     for dt in (torch.uint8, torch.float16, torch.bfloat16):
         xs = (x * 255).to(torch.uint8) if dt == torch.uint8 else x.to(dt)
-        pad = torch.zeros(2, 203, 513, device=DEV, dtype=dt)
-        pad[:, :, :512] = xs
-        xv = pad[:, :, :512]  # row stride 513 elements: register path
-        for r in (0, 1, 7, 64, 100):
-            a = api.zoom2x_fwd(xs, rows_per_tile=r)
-            b = api.zoom2x_fwd(xv, rows_per_tile=r)
-            torch.cuda.synchronize()
-            assert torch.equal(a, b), (dt, r)
+        for img in (xs[:, :, :512].contiguous(), xs, xs[:, :, :511]):
+            xv = _register_path_copy(img)
+            for r in (0, 1, 7, 64, 100):
+                a = api.zoom2x_fwd(img, rows_per_tile=r)
+                b = api.zoom2x_fwd(xv, rows_per_tile=r)
+                torch.cuda.synchronize()
+                assert torch.equal(a, b), (dt, tuple(img.shape), img.stride(), r)
+
+
+@pytest.mark.parametrize("dt", ["u8", "f16", "bf16"])
+def test_fwd_unaligned_rows_and_views(dt):
+    """Bulk copies of rows that start anywhere: odd widths, a crop that starts
+    at an odd element of an odd row, and single columns; parity with the
+    oracle."""
+    for shape in [(3, 1), (7, 13), (41, 257), (33, 499), (19, 771)]:
+        A = RNG.random((2,) + shape)
+        out, ref = _run(A, dt, dt)
+        parity.compare(out, ref, dt)
+    big = RNG.random((2, 61, 530))
+    xb = parity.encode(big, dt).to(DEV)
+    view = xb[:, 3:58, 5:522]  # base, rows and planes all off 16-byte boundaries
+    out = api.zoom2x_fwd(view)
+    torch.cuda.synchronize()
+    ref = parity.oracle_planes(parity.decode(view.cpu()), api.Params())
+    parity.compare(out, ref, dt)
 
 
 def test_fwd_no_abandoned_waits():
