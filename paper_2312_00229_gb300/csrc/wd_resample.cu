@@ -186,29 +186,26 @@ __global__ void __launch_bounds__(RS_THREADS) resample_tiled_kernel(ResampleArgs
   const int64_t plane = blockIdx.z;
   const int nc = (int)(a.m_out - c0 < RS_TC ? a.m_out - c0 : RS_TC);
   const int nr = (int)(a.n_out - r0 < RS_TR ? a.n_out - r0 : RS_TR);
-  int64_t jf, jl, i_first, i_last;
-  float tdummy;
-  grid_pos(c0, a.m, a.m_out, a.div_x, jf, tdummy);
-  grid_pos(c0 + nc - 1, a.m, a.m_out, a.div_x, jl, tdummy);
-  grid_pos(r0, a.n, a.n_out, a.div_y, i_first, tdummy);
-  grid_pos(r0 + nr - 1, a.n, a.n_out, a.div_y, i_last, tdummy);
-  const int64_t kfirst = jf - 1, ifirst = i_first - 1;
-  const int wc = (int)(jl + 2 - kfirst + 1);       // <= RS_WC (host checks the x scale)
-  const int wr = (int)(i_last + 2 - ifirst + 1);   // <= a.win_rows (host sizes it)
+  // Every output column's and row's cell index (absolute) and offset; the
+  // first and last of them bound the input window.
   if (tid < nc) {
     int64_t j;
     float t;
     grid_pos(c0 + tid, a.m, a.m_out, a.div_x, j, t);
-    col_j[tid] = (int)(j - 1 - kfirst);
+    col_j[tid] = (int)j;
     col_t[tid] = t;
   }
   if (tid >= RS_TC && tid - RS_TC < nr) {
     int64_t i;
     float t;
     grid_pos(r0 + tid - RS_TC, a.n, a.n_out, a.div_y, i, t);
-    row_i[tid - RS_TC] = (int)(i - 1 - ifirst);
+    row_i[tid - RS_TC] = (int)i;
     row_t[tid - RS_TC] = t;
   }
+  __syncthreads();
+  const int64_t kfirst = (int64_t)col_j[0] - 1, ifirst = (int64_t)row_i[0] - 1;
+  const int wc = col_j[nc - 1] + 2 - (int)kfirst + 1;  // <= RS_WC (host checks the x scale)
+  const int wr = row_i[nr - 1] + 2 - (int)ifirst + 1;  // <= a.win_rows (host sizes it)
   // stage 0: decoded, clamped input window
   const int64_t pbase = plane * a.in_sc;
   for (int rr = warp; rr < wr; rr += RS_THREADS / 32) {
@@ -224,7 +221,7 @@ __global__ void __launch_bounds__(RS_THREADS) resample_tiled_kernel(ResampleArgs
   __syncthreads();
   // pass 1: column interpolants
   for (int r = warp; r < nr; r += RS_THREADS / 32) {
-    const float* w0 = win[row_i[r]];
+    const float* w0 = win[row_i[r] - 1 - (int)ifirst];
     if (a.n > 1) {
       const float ty = row_t[r];
       const float C0 = (2.f - ty) * (1.f / 3.f), h = 0.5f * fmaf(ty, ty, -ty);
@@ -246,7 +243,7 @@ __global__ void __launch_bounds__(RS_THREADS) resample_tiled_kernel(ResampleArgs
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const int cc = c + (q < cn ? q : 0);  // columns past the tile repeat the first (not stored)
-    kq[q] = col_j[cc];
+    kq[q] = col_j[cc] - 1 - (int)kfirst;
     tq[q] = col_t[cc];
     cq[q] = (2.f - tq[q]) * (1.f / 3.f);
     hq[q] = 0.5f * fmaf(tq[q], tq[q], -tq[q]);
