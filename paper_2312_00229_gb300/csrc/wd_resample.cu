@@ -165,7 +165,7 @@ __device__ __forceinline__ void rs_store4(void* base, int64_t idx, const float (
 //            the z values (Eq. tensor, second factor) and stores them together
 // Per output this is 1 + (in/out column ratio) + halo 1-D interpolants
 // instead of 5.
-constexpr int RS_TR = 16;
+constexpr int RS_TR = 32;
 constexpr int RS_TC = 128;
 constexpr int RS_WC = 2 * RS_TC + 8;  // window columns (>= 2 (RS_TC - 1) + 5)
 constexpr int RS_THREADS = 256;
