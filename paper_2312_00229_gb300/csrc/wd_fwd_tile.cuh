@@ -36,16 +36,16 @@
 // One barrier (B1) opens each step: every shared value a step reads was
 // written in an earlier step, in a slot no thread writes in the same step.
 //
-// Input path.  For 1- and 2-byte storage with unit column stride
-// (FwdArgs::in_bulk), thread 0 requests each input row segment of the strip
-// (with its halo; the 16-byte blocks that cover it) KAHEAD steps ahead as one
-// asynchronous bulk copy into a ring of RING raw rows in shared memory,
-// completing on the slot's mbarrier.  At the end of
-// step s every thread waits for row s and decodes its own (clamped) column of
-// it into the float ring (first read in step s+1).  The sweep's barriers do
-// not wait for these copies, unlike register loads issued before them, so the
-// DRAM latency is covered by KAHEAD steps of work.  Other layouts (INB = false) load each row into a
-// register two steps ahead.
+// Input path (template parameter INB, see InputPath).  For 1- and 2-byte
+// storage with unit column stride, thread 0 requests each input row segment
+// of the strip (with its halo; the 16-byte blocks that cover it) KAHEAD steps
+// ahead as one asynchronous bulk copy into a ring of RING raw rows in shared
+// memory, completing on the slot's mbarrier.  At the end of step s every
+// thread waits for row s and decodes its own (clamped) column of it into the
+// float ring (first read in step s+1).  The sweep's barriers do not wait for
+// these copies, unlike register loads issued before them, so the DRAM latency
+// is covered by KAHEAD steps of work.  FP32 and strided columns (IN_REG) load
+// each row into a register two steps ahead.
 #pragma once
 
 #include <cstddef>
