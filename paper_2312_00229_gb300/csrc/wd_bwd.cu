@@ -23,9 +23,9 @@
 //   k_psi      phase-2 indicators of every E and S point
 //   k_padj     p_bar, D_bar of the "+" points that receive an output gradient
 //   k_coef<T>  per stencil and node role, the coefficient above
-//   k_gather2  X_bar (plus the x-point output gradient) and A_bar from
-//              phase 2 (plus the sample-point output gradient)
-//   k_xadj     p_bar, D_bar of the x points
+//   k_gather2_xadj  X_bar (plus the x-point output gradient) and A_bar from
+//              phase 2 (plus the sample-point output gradient), then the
+//              x point's p_bar, D_bar from that X_bar
 //   k_gather1  A_bar += phase-1 contributions
 //   k_fold     grad_in = A_bar summed over each pixel's clamp preimage
 #include "wd_bwd.h"
@@ -52,7 +52,7 @@ enum VGroup {
 enum Slot {
   S_X = 0,     // phase-1 values
   S_AB = 1,    // A_bar on the extended grid
-  S_XB = 2,    // X_bar
+  S_XB = 2,    // (unused: X_bar is consumed where it is gathered)
   S_ECO = 3,   // 12: E coefficients, index k*3 + t   (phase 1 reuses for x)
   S_SCO = 15,  // 12: S coefficients
   S_A = 27,    // the input, clamp-extended to the work grid
@@ -425,7 +425,12 @@ __device__ __forceinline__ float gather(const Ctx& c, int type, int lattice, int
   return acc;
 }
 
-__global__ void k_gather2(BwdArgs a, MethodConsts k) {
+// X_bar (plus the x-point output gradient) and A_bar from phase 2, then at
+// once the x point's own adjoint from that X_bar (phase 1): p_bar, D_bar of
+// the x points, into the groups the "+" points used (no thread of this
+// kernel reads them).
+template <int BMODE>
+__global__ void k_gather2_xadj(BwdArgs a, MethodConsts k) {
   Ctx c; int I, J;
   if (!setup(a, k, c, I, J)) return;
   const int64_t plane = blockIdx.z;
@@ -435,24 +440,16 @@ __global__ void k_gather2(BwdArgs a, MethodConsts k) {
     xb += gout_at(a, plane, 2 * (int64_t)I + 1, 2 * (int64_t)J + 1);
     ab += gout_at(a, plane, 2 * (int64_t)I, 2 * (int64_t)J);
   }
-  W(c, S_XB, I, J) = xb;
   W(c, S_AB, I, J) = ab;
-}
-
-// ---- phase-1 adjoint ----------------------------------------------------------
-template <int BMODE>
-__global__ void k_xadj(BwdArgs a, MethodConsts k) {
-  Ctx c; int I, J;
-  if (!setup(a, k, c, I, J)) return;
+  // ---- phase-1 adjoint of this x point ----
   float pX[4] = {0.f, 0.f, 0.f, 0.f}, dX[4] = {0.f, 0.f, 0.f, 0.f};
-  const float xb = W(c, S_XB, I, J);
   if (xb != 0.f && I >= -4 && I < c.n + 4 && J >= -4 && J < c.m + 4) {
     const Pt q = eval_pt(c, 0, I, J);
     float D[4];
     d_x<BMODE>(c, I, J, q.si, D);
     point_adjoint<BMODE>(q, D, c.beta, xb, pX, dX);
   }
-  V(c, G_EP, I, J) = f4(pX);  // groups reused for x points
+  V(c, G_EP, I, J) = f4(pX);
   V(c, G_ED, I, J) = f4(dX);
 }
 
@@ -497,8 +494,7 @@ cudaError_t launch_all(const BwdArgs& a, const MethodConsts& k, cudaStream_t st)
   k_psi<<<grid, block, 0, st>>>(a, k);
   k_padj<BMODE><<<grid, block, 0, st>>>(a, k);
   k_coef2<<<grid, block, 0, st>>>(a, k);
-  k_gather2<<<grid, block, 0, st>>>(a, k);
-  k_xadj<BMODE><<<grid, block, 0, st>>>(a, k);
+  k_gather2_xadj<BMODE><<<grid, block, 0, st>>>(a, k);
   k_coef1<<<grid, block, 0, st>>>(a, k);
   k_gather1<<<grid, block, 0, st>>>(a, k);
   k_fold<<<grid, block, 0, st>>>(a, k);
