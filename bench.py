@@ -87,11 +87,20 @@ def peaks():
     return 6800.0, 2070.0, "fallback"
 
 
+def _code_only(text: str) -> str:
+    """C++ source without comments and with whitespace collapsed, so that a
+    comment edit does not read as a kernel change."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def kernel_sha():
+    """Hash of the forward kernel's code (comments and layout ignored)."""
     h = hashlib.sha256()
     for rel in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, rel), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, rel), encoding="utf-8") as fh:
+            h.update(_code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 
