@@ -117,7 +117,7 @@ int weno_zoom2x_bwd(const weno_image* x, const weno_image* grad_out,
                     size_t workspace_bytes, void* stream);
 
 /* Scratch bytes weno_zoom2x_bwd needs for an input shaped like `x`
- * (56 FP32 values per cell of the image extended by 7 cells per side, per
+ * (55 FP32 values per cell of the image extended by 7 cells per side, per
  * channel, the cell count rounded up to a multiple of 4).  Returns 0 for a
  * malformed descriptor. */
 size_t weno_zoom2x_bwd_workspace_bytes(const weno_image* x);

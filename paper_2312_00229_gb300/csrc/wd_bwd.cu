@@ -52,11 +52,10 @@ enum VGroup {
 enum Slot {
   S_X = 0,     // phase-1 values
   S_AB = 1,    // A_bar on the extended grid
-  S_XB = 2,    // (unused: X_bar is consumed where it is gathered)
-  S_ECO = 3,   // 12: E coefficients, index k*3 + t   (phase 1 reuses for x)
-  S_SCO = 15,  // 12: S coefficients
-  S_A = 27,    // the input, clamp-extended to the work grid
-  S_N = 28
+  S_ECO = 2,   // 12: E coefficients, index k*3 + t   (phase 1 reuses for x)
+  S_SCO = 14,  // 12: S coefficients
+  S_A = 26,    // the input, clamp-extended to the work grid
+  S_N = 27
 };
 static_assert(4 * G_N + S_N == BWD_ARRAYS, "workspace slot count");
 

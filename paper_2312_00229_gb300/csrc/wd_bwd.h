@@ -10,7 +10,7 @@
 namespace wdweno {
 
 constexpr int BWD_GHOST = 7;    // extension cells per side of the work grid
-constexpr int BWD_ARRAYS = 56;  // FP32 arrays per plane in the workspace
+constexpr int BWD_ARRAYS = 55;  // FP32 arrays per plane in the workspace
 
 struct BwdArgs {
   const float* x;

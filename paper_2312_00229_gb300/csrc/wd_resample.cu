@@ -156,7 +156,8 @@ __device__ __forceinline__ void rs_store4(void* base, int64_t idx, const float (
 }
 
 // Separable tiled form for output/input spacing ratios down to 1/2 on both
-// axes: a CTA owns RS_TR output rows x RS_TC output columns of one plane.
+// axes: a CTA owns tile_rows (16 or 32) output rows x RS_TC output columns of one
+// plane.
 //   stage 0  the input window those outputs read (rows i(r0)-1 .. i(r_last)+2,
 //            columns j(c0)-1 .. j(c_last)+2, clamped) decoded into shared memory
 //   pass 1   the column interpolants z(r, k) = w(A(:, k), y_r) of the tile's
@@ -165,7 +166,12 @@ __device__ __forceinline__ void rs_store4(void* base, int64_t idx, const float (
 //            the z values (Eq. tensor, second factor) and stores them together
 // Per output this is 1 + (in/out column ratio) + halo 1-D interpolants
 // instead of 5.
-constexpr int RS_TR = 32;
+// Output rows per tile: 32 when the rows are magnified (the per-tile setup
+// and window decode spread over more outputs), 16 when they are reduced (the
+// window then has up to twice the tile's rows, and taller tiles would leave
+// fewer CTAs per SM).
+constexpr int RS_TR_UP = 32;
+constexpr int RS_TR_DOWN = 16;
 constexpr int RS_TC = 128;
 constexpr int RS_WC = 2 * RS_TC + 8;  // window columns (>= 2 (RS_TC - 1) + 5)
 constexpr int RS_THREADS = 256;
@@ -175,17 +181,18 @@ __global__ void __launch_bounds__(RS_THREADS) resample_tiled_kernel(ResampleArgs
                                                                    float beta) {
   extern __shared__ float rs_smem[];
   float(*win)[RS_WC] = reinterpret_cast<float(*)[RS_WC]>(rs_smem);               // a.win_rows
-  float(*z)[RS_WC] = reinterpret_cast<float(*)[RS_WC]>(rs_smem + a.win_rows * RS_WC);  // RS_TR
+  float(*z)[RS_WC] = reinterpret_cast<float(*)[RS_WC]>(rs_smem + a.win_rows * RS_WC);  // tile_rows
   __shared__ int col_j[RS_TC];
   __shared__ float col_t[RS_TC];
-  __shared__ int row_i[RS_TR];
-  __shared__ float row_t[RS_TR];
+  __shared__ int row_i[RS_TR_UP];
+  __shared__ float row_t[RS_TR_UP];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t c0 = (int64_t)blockIdx.x * RS_TC;
-  const int64_t r0 = (int64_t)blockIdx.y * RS_TR;
+  const int tr = a.tile_rows;
+  const int64_t r0 = (int64_t)blockIdx.y * tr;
   const int64_t plane = blockIdx.z;
   const int nc = (int)(a.m_out - c0 < RS_TC ? a.m_out - c0 : RS_TC);
-  const int nr = (int)(a.n_out - r0 < RS_TR ? a.n_out - r0 : RS_TR);
+  const int nr = (int)(a.n_out - r0 < tr ? a.n_out - r0 : tr);
   // Every output column's and row's cell index (absolute) and offset; the
   // first and last of them bound the input window.
   if (tid < nc) {
@@ -271,7 +278,7 @@ __global__ void __launch_bounds__(RS_THREADS) resample_tiled_kernel(ResampleArgs
 
 template <int BMODE, class TIn, class TOut>
 cudaError_t launch_tiled(const ResampleArgs& a, float eps, float beta, cudaStream_t stream) {
-  const size_t smem = (size_t)(a.win_rows + RS_TR) * RS_WC * sizeof(float);
+  const size_t smem = (size_t)(a.win_rows + a.tile_rows) * RS_WC * sizeof(float);
   auto kern = resample_tiled_kernel<BMODE, TIn, TOut>;
   if (smem > 48 * 1024) {
     cudaError_t e =
@@ -279,7 +286,7 @@ cudaError_t launch_tiled(const ResampleArgs& a, float eps, float beta, cudaStrea
     if (e != cudaSuccess) return e;
   }
   const dim3 grid((unsigned)((a.m_out + RS_TC - 1) / RS_TC),
-                  (unsigned)((a.n_out + RS_TR - 1) / RS_TR), (unsigned)a.planes);
+                  (unsigned)((a.n_out + a.tile_rows - 1) / a.tile_rows), (unsigned)a.planes);
   kern<<<grid, RS_THREADS, smem, stream>>>(a, eps, beta);
   return cudaGetLastError();
 }
@@ -325,7 +332,9 @@ cudaError_t launch_resample(const ResampleArgs& a_in, float eps, float beta, int
   const bool tiled = (a.m_out == 1 || 2 * (a.m_out - 1) >= (a.m - 1)) &&
                      (a.n_out == 1 || 2 * (a.n_out - 1) >= (a.n - 1));
   if (tiled) {
-    a.win_rows = (a.n_out > 1 ? (int)((int64_t)(RS_TR - 1) * (a.n - 1) / (a.n_out - 1)) : 0) + 5;
+    a.tile_rows = a.n_out >= a.n ? RS_TR_UP : RS_TR_DOWN;
+    a.win_rows =
+        (a.n_out > 1 ? (int)((int64_t)(a.tile_rows - 1) * (a.n - 1) / (a.n_out - 1)) : 0) + 5;
     const int i = a.in_dtype, o = a.out_dtype;
     if (i == DT_U8 && o == DT_U8) return launch_tiled_beta<uint8_t, uint8_t>(a, eps, beta, bmode, stream);
     if (i == DT_F16 && o == DT_F16) return launch_tiled_beta<__half, __half>(a, eps, beta, bmode, stream);

@@ -33,6 +33,7 @@ struct ResampleArgs {
   int out_vec4;                  // unit column stride, rows and planes of 4-element
                                  // multiples, 4-element aligned base
   int win_rows;                  // window rows of the tiled kernel (set by the launcher)
+  int tile_rows;                 // output rows per tile of the tiled kernel (launcher)
   AxisDiv div_y, div_x;          // division by n_out - 1, m_out - 1 (set by the launcher)
 };
 

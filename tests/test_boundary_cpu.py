@@ -97,7 +97,7 @@ def test_bwd_rejects_bad_arguments_without_launching():
     go = _img(FAKE_OUT, 8, 10, 1)
     gi = _img(0x30000000, 4, 5, 1)
     need = B.weno_zoom2x_bwd_workspace_bytes(x)
-    assert need == 4 * 56 * (((4 + 14) * (5 + 14) + 3) // 4 * 4)  # cells padded to a multiple of 4
+    assert need == 4 * 55 * (((4 + 14) * (5 + 14) + 3) // 4 * 4)  # cells padded to a multiple of 4
     assert B.weno_zoom2x_bwd(x, go, gi, p, None, need, None) == B.WENO_EWORKSPACE
     assert B.weno_zoom2x_bwd(x, go, gi, p, 0x40000000, need - 1, None) == B.WENO_EWORKSPACE
     assert B.weno_zoom2x_bwd(x, go, gi, p, 0x40000004, need, None) == B.WENO_EWORKSPACE
