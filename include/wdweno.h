@@ -72,6 +72,15 @@ typedef struct {
   int out_mode;    /* weno_out_mode; default WENO_OUT_2N */
   int clamp_float; /* 1: saturate float outputs to [0, 1]; default 0.
                       uint8 outputs always saturate. */
+  float data_bound; /* 0 (default): unknown.  Otherwise the caller guarantees
+                       |input value| <= data_bound (after decoding; uint8 is
+                       v / 255).  This changes no result beyond rounding: it
+                       lets the library take the beta = 2 weights of Eq.
+                       (alpha) as 1 / D^2 directly for any storage type, where
+                       it proves that every weight stays in the FP32 range (as
+                       it does from the type alone for uint8 and FP16).  A
+                       bound that the data exceed can overflow the weights
+                       (inf / NaN outputs).  Must be >= 0 and finite. */
 } weno_params;
 
 /* One image: `channels` planes of height x width. */
@@ -81,7 +90,8 @@ typedef struct {
   int64_t stride_c, stride_h, stride_w; /* element strides, all > 0 */
 } weno_image;
 
-/* Defaults: beta 2, k_eps 1e-8, h 1, normalized SI, 2n x 2m, no clamp. */
+/* Defaults: beta 2, k_eps 1e-8, h 1, normalized SI, 2n x 2m, no clamp,
+ * data_bound 0 (unknown). */
 weno_params weno_params_default(void);
 
 /* Human-readable text of a status code (static storage). */

@@ -30,6 +30,8 @@ class Params:
     si_scale : 0 normalized indicator length scale, 1 literal sqrt(2) h
     out_mode : 0 -> 2n x 2m output, 1 -> (2n-1) x (2m-1) (Sec. 3)
     clamp_float : saturate float outputs to [0, 1]
+    data_bound : 0, or a bound on |input| the caller guarantees (lets the
+                 library take the direct beta = 2 weights for FP32/BF16 data)
     """
     beta: float = 2.0
     k_eps: float = 1e-8
@@ -37,12 +39,14 @@ class Params:
     si_scale: int = B.WENO_SI_NORMALIZED
     out_mode: int = B.WENO_OUT_2N
     clamp_float: bool = False
+    data_bound: float = 0.0
 
     def c(self) -> B.weno_params:
         p = B.weno_params()
         p.beta, p.k_eps, p.h = float(self.beta), float(self.k_eps), float(self.h)
         p.si_scale, p.out_mode, p.clamp_float = int(self.si_scale), int(self.out_mode), int(
             bool(self.clamp_float))
+        p.data_bound = float(self.data_bound)
         return p
 
 
@@ -175,17 +179,38 @@ def zoom2x(x: torch.Tensor, params: Optional[Params] = None, out_dtype=None,
     return zoom2x_fwd(x, params, out_dtype=out_dtype, layout=layout)
 
 
+_TYPE_BOUND = {torch.uint8: 1.0, torch.float16: 65504.0}
+# One 2x level maps data bounded by M to data bounded by 1.5625 M: an x value
+# is a convex combination of quadratic interpolants (|p| <= 1.25 max|node|),
+# and a "+" value one of interpolants whose nodes include x values.  The
+# factor carries slack for the rounding of the weights.
+_LEVEL_GROWTH = 1.5625 * (1.0 + 1e-3)
+
+
+def _level_bounds(x: torch.Tensor, params: Params, levels: int):
+    """Bound on |input| of each level of a chain of 2x zooms (and of the
+    level after the last), from the input's storage type and the caller's
+    ``data_bound``; 0 where neither bounds the data."""
+    b0 = _TYPE_BOUND.get(x.dtype, 0.0)
+    if params.data_bound > 0 and (b0 == 0.0 or params.data_bound < b0):
+        b0 = float(params.data_bound)
+    return [b0 * _LEVEL_GROWTH ** lvl for lvl in range(levels + 1)]
+
+
 def cascade_zoom(x: torch.Tensor, levels: int, params: Optional[Params] = None, out_dtype=None,
                  inter_dtype=torch.float32, layout: str = "chw") -> torch.Tensor:
     """``levels`` successive 2x zooms (Sec. 3.3, Eq. zoomfactor); the
     intermediate images are kept in ``inter_dtype`` and only the last one is
     encoded to ``out_dtype``.  Each level's coarse grid is the previous
-    level's fine grid, so its spacing ``h`` is half the previous one."""
+    level's fine grid, so its spacing ``h`` is half the previous one.  The
+    bound the input's type gives is carried to the later levels
+    (``data_bound``), so FP32 intermediates keep the direct weights."""
     params = params or Params()
+    bounds = _level_bounds(x, params, levels)
     cur = x
     for lvl in range(levels):
         last = lvl == levels - 1
-        p = dataclasses.replace(params, h=params.h / (1 << lvl))
+        p = dataclasses.replace(params, h=params.h / (1 << lvl), data_bound=bounds[lvl])
         cur = zoom2x_fwd(cur, p, out_dtype=(out_dtype or x.dtype) if last else inter_dtype,
                          layout=layout)
     return cur
@@ -238,12 +263,15 @@ def zoom_to(x: torch.Tensor, out_h: int, out_w: int, params: Optional[Params] = 
     params = params or Params()
     n, m = _hw(x, layout)
     k = zoom_levels(n, m, out_h, out_w)
+    bounds = _level_bounds(x, params, k)
     cur = x
     p = dataclasses.replace(params, out_mode=B.WENO_OUT_2N_MINUS_1)
     for lvl in range(k):
-        cur = zoom2x_fwd(cur, dataclasses.replace(p, h=params.h / (1 << lvl)),
+        cur = zoom2x_fwd(cur, dataclasses.replace(p, h=params.h / (1 << lvl),
+                                                  data_bound=bounds[lvl]),
                          out_dtype=inter_dtype, layout=layout)
-    return resample(cur, out_h, out_w, dataclasses.replace(params, h=params.h / (1 << k)),
+    return resample(cur, out_h, out_w,
+                    dataclasses.replace(params, h=params.h / (1 << k), data_bound=bounds[k]),
                     out_dtype=out_dtype or x.dtype, layout=layout)
 
 

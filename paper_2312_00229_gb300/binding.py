@@ -42,6 +42,7 @@ class weno_params(ctypes.Structure):
         ("si_scale", ctypes.c_int),
         ("out_mode", ctypes.c_int),
         ("clamp_float", ctypes.c_int),
+        ("data_bound", ctypes.c_float),
     ]
 
 

@@ -69,14 +69,21 @@ def build(force: bool = False, verbose: bool = False, extra_flags=(), lib_path=N
         return obj
 
     srcs = _sources()
-    with cf.ThreadPoolExecutor(max_workers=len(srcs)) as ex:
-        objs = list(ex.map(compile_one, srcs))
-    tmp = target + f".tmp{os.getpid()}"
-    cmd = [cc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, target)
+    objs = [os.path.join(os.path.dirname(target), s.replace(".cu", f".{os.getpid()}.o"))
+            for s in srcs]
+    try:
+        with cf.ThreadPoolExecutor(max_workers=len(srcs)) as ex:
+            list(ex.map(compile_one, srcs))
+        tmp = target + f".tmp{os.getpid()}"
+        cmd = [cc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+        os.replace(tmp, target)
+    finally:
+        for o in objs:  # the per-process object files are not kept
+            if os.path.exists(o):
+                os.remove(o)
     return target
 
 

@@ -98,7 +98,8 @@ bool overlaps(const weno_image* a, int64_t ea, const weno_image* b, int64_t eb) 
 // (2DsmoothnessFinal)/(tezine) into per-SI constants (see MethodConsts).
 bool fold_consts(const weno_params& p, MethodConsts* k, int* bmode) {
   if (!(p.beta >= 0.f) || !(p.k_eps >= 0.f) || !(p.h > 0.f) || !std::isfinite(p.beta) ||
-      !std::isfinite(p.k_eps) || !std::isfinite(p.h))
+      !std::isfinite(p.k_eps) || !std::isfinite(p.h) || !(p.data_bound >= 0.f) ||
+      !std::isfinite(p.data_bound))
     return false;
   if (p.si_scale != WENO_SI_NORMALIZED && p.si_scale != WENO_SI_LITERAL_SQRT2H) return false;
   const double h = p.h;
@@ -133,23 +134,26 @@ bool fold_consts(const weno_params& p, MethodConsts* k, int* bmode) {
 // as 1 / D^2 directly (B2R) instead of the scale-free (D_min / D)^2.  That
 // needs every D inside [lo, hi] with 1/hi^2 and 1/lo^2 normal FP32 numbers,
 // and the weight sum and the blend numerator finite.  The storage type
-// bounds the data: |input| <= v0 (uint8 decodes to [0, 1]; FP16 <= 65504).
+// bounds the data (uint8 decodes to [0, 1]; FP16 <= 65504), or the caller
+// does through weno_params::data_bound: |input| <= v0.
 // Every node of an interpolant is an input or a phase-1 value, a convex
 // combination of quadratic interpolants (|p| <= 1.25 max |node|), so
 // |node| <= v = 1.25 v0; then |g| <= 2v, |s| <= 4v and
 //   SI <= 4 v^2 + (25/12) 16 v^2 + eps_h,  D <= (1 + 4w) SI_max,
 //   D >= eps_h / sqrt(2) (phase 2 of the literal SI scaling; eps_h otherwise).
 // The weights are at most 1/lo^2 each, the numerator at most 16 v times their
-// largest value.  BFloat16 and FP32 data are unbounded: they keep B2.
+// largest value.  BFloat16 and FP32 data without a caller's bound keep B2.
+// Bound on |input| from the storage type (uint8, FP16) or from the caller's
+// weno_params::data_bound, the smaller when both hold; 0 when neither does.
+double input_bound(const weno_params& p, int in_t) {
+  double v0 = in_t == WENO_U8 ? 1.0 : (in_t == WENO_F16 ? 65504.0 : 0.0);
+  if (p.data_bound > 0.f && (v0 == 0.0 || double(p.data_bound) < v0)) v0 = p.data_bound;
+  return v0;
+}
+
 bool direct_b2_ok(const weno_params& p, int in_t) {
-  double v0;
-  if (in_t == WENO_U8) {
-    v0 = 1.0;
-  } else if (in_t == WENO_F16) {
-    v0 = 65504.0;
-  } else {
-    return false;
-  }
+  const double v0 = input_bound(p, in_t);
+  if (!(v0 > 0.0)) return false;
   const double h = p.h, w = h * h / 4.0, eps_h = double(p.k_eps) * h * h;
   const double v = 1.25 * v0 * (1.0 + 1e-3);  // slack for the approximate reciprocals
   const double si_max = 4.0 * v * v + 25.0 / 12.0 * 16.0 * v * v + eps_h;
@@ -165,15 +169,9 @@ bool direct_b2_ok(const weno_params& p, int in_t) {
 // as written needs eps^2 normal and (e_max)^2 times the largest |s| finite.
 // The nodes are inputs or first-pass values, quadratic interpolants on
 // [0, 1] of inputs (|p| <= 1.25 max|node|).
-bool resample_direct_ok(int in_t, double eps) {
-  double v0;
-  if (in_t == WENO_U8) {
-    v0 = 1.0;
-  } else if (in_t == WENO_F16) {
-    v0 = 65504.0;
-  } else {
-    return false;
-  }
+bool resample_direct_ok(const weno_params& p, int in_t, double eps) {
+  const double v0 = input_bound(p, in_t);
+  if (!(v0 > 0.0)) return false;
   const double v = 1.25 * v0 * (1.0 + 1e-3);
   const double e_hi = 4.0 * v * v + 13.0 / 12.0 * 16.0 * v * v + eps;
   return eps >= 1e-18 && e_hi <= 1e18 && e_hi * e_hi * 4.0 * v <= 1e37;
@@ -233,6 +231,7 @@ weno_params weno_params_default(void) {
   p.si_scale = WENO_SI_NORMALIZED;
   p.out_mode = WENO_OUT_2N;
   p.clamp_float = 0;
+  p.data_bound = 0.f;
   return p;
 }
 
@@ -385,7 +384,7 @@ int weno_resample(const weno_image* in, weno_dtype in_t, const weno_image* out,
   a.win_rows = 0;
   // a floor of 1e-30 keeps the larger indicator a normal FP32 number
   const float eps = std::max(float(double(p.k_eps) * double(p.h) * double(p.h)), 1e-30f);
-  if (bmode == B2 && resample_direct_ok(in_t, eps)) bmode = B2R;
+  if (bmode == B2 && resample_direct_ok(p, in_t, eps)) bmode = B2R;
   cudaError_t e = launch_resample(a, eps, p.beta, bmode, static_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? WENO_OK : WENO_ECUDA;
 }

@@ -209,11 +209,13 @@ cudaError_t launch_zoom2x_batched(const BatchedArgs& a, const MethodConsts& k, i
   batched_setup_kernel<<<1, SETUP_THREADS, 0, stream>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  if (bmode == B2R) {  // only for storage types that bound the data
+  if (bmode == B2R) {  // data bounded by the storage type or the caller's bound
     if (a.in_dtype == DT_U8 && a.out_dtype == DT_U8)
       return launch_persistent<B2R, TypedIO<uint8_t, uint8_t>>(a, k, stream);
     if (a.in_dtype == DT_F16 && a.out_dtype == DT_F16)
       return launch_persistent<B2R, TypedIO<__half, __half>>(a, k, stream);
+    if (a.in_dtype == DT_F32 && a.out_dtype == DT_F32)
+      return launch_persistent<B2R, TypedIO<float, float>>(a, k, stream);
     return launch_persistent<B2R, DynIO>(a, k, stream);
   }
   if (bmode == B2 && a.in_dtype == a.out_dtype) {

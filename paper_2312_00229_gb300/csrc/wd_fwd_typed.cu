@@ -1,6 +1,7 @@
 // Forward kernels with the storage types fixed at compile time (beta = 2):
 // the same-type pairs and the uint8 <-> FP32 pairs of a cascade, and the
-// direct 1/D^2 weights (B2R) for the pairs whose input type bounds the data.
+// direct 1/D^2 weights (B2R) for the common pairs, used when the data are
+// bounded (by the input type or by the caller's weno_params::data_bound).
 #include "wd_fwd_kernels.cuh"
 
 namespace wdweno {
@@ -11,10 +12,14 @@ cudaError_t launch_fwd_typed(const FwdArgs& a, const MethodConsts& k, int bmode,
   using fwd_tile::TypedIO;
   *handled = true;
   const int i = a.in_dtype, o = a.out_dtype;
-  if (bmode == B2R) {  // only for storage types that bound the data
+  if (bmode == B2R) {  // data bounded by the storage type or the caller's bound
     if (i == DT_U8 && o == DT_U8) return launch_fwd<B2R, TypedIO<uint8_t, uint8_t>>(a, k, stream);
     if (i == DT_F16 && o == DT_F16) return launch_fwd<B2R, TypedIO<__half, __half>>(a, k, stream);
     if (i == DT_U8 && o == DT_F32) return launch_fwd<B2R, TypedIO<uint8_t, float>>(a, k, stream);
+    if (i == DT_F32 && o == DT_F32) return launch_fwd<B2R, TypedIO<float, float>>(a, k, stream);
+    if (i == DT_F32 && o == DT_U8) return launch_fwd<B2R, TypedIO<float, uint8_t>>(a, k, stream);
+    if (i == DT_BF16 && o == DT_BF16)
+      return launch_fwd<B2R, TypedIO<__nv_bfloat16, __nv_bfloat16>>(a, k, stream);
     *handled = false;
     return cudaSuccess;
   }

@@ -34,8 +34,8 @@ def test_library_exports_every_declared_symbol():
 
 def test_params_default():
     p = B.weno_params_default()
-    assert (p.beta, p.k_eps, p.h, p.si_scale, p.out_mode, p.clamp_float) == (
-        pytest.approx(2.0), pytest.approx(1e-8), pytest.approx(1.0), 0, 0, 0)
+    assert (p.beta, p.k_eps, p.h, p.si_scale, p.out_mode, p.clamp_float, p.data_bound) == (
+        pytest.approx(2.0), pytest.approx(1e-8), pytest.approx(1.0), 0, 0, 0, 0.0)
 
 
 def test_status_strings():
@@ -82,6 +82,10 @@ def test_fwd_rejects_bad_arguments_without_launching():
     bad = B.weno_params_default()
     bad.out_mode = 5
     assert B.weno_zoom2x_fwd(good_in, 0, good_out, 0, bad, None) == B.WENO_EINVAL
+    for v in (-1.0, float("inf"), float("nan")):  # data_bound must be finite and >= 0
+        bad = B.weno_params_default()
+        bad.data_bound = v
+        assert B.weno_zoom2x_fwd(good_in, 0, good_out, 0, bad, None) == B.WENO_EINVAL
     # (2n-1) mode changes the expected output shape
     m1 = B.weno_params_default()
     m1.out_mode = 1

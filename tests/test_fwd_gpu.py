@@ -295,3 +295,24 @@ def test_fwd_direct_and_scale_free_weights_agree():
     b = api.zoom2x_fwd(x.float(), out_dtype=torch.float32)
     torch.cuda.synchronize()
     assert (a - b).abs().max().item() <= 4e-6
+
+
+def test_fwd_data_bound_selects_direct_weights():
+    """FP32 data with a caller-given bound take the direct 1/D^2 weights:
+    parity with the oracle, agreement with the scale-free weights (no bound)
+    to a few FP32 rounding steps, and a bound too large for the range proof
+    (1e30) falls back to the scale-free form with the same parity."""
+    A = RNG.random((2, 53, 301))
+    for bound in (1.0, 7.5, 1e30):
+        out, ref = _run(A, "f32", "f32", api.Params(data_bound=bound))
+        parity.compare(out, ref, "f32")
+    x = torch.from_numpy(A.astype(np.float32)).to(DEV)
+    a = api.zoom2x_fwd(x, api.Params(data_bound=1.0))
+    b = api.zoom2x_fwd(x)
+    torch.cuda.synchronize()
+    assert (a - b).abs().max().item() <= 4e-6
+    big = torch.from_numpy((A * 2e3 - 1e3).astype(np.float32))
+    out = api.zoom2x_fwd(big.to(DEV), api.Params(data_bound=1e3))
+    torch.cuda.synchronize()
+    ref = parity.oracle_planes(big.double().numpy(), api.Params())
+    parity.compare(out, ref, "f32", value_range=float(ref.max() - ref.min()))
