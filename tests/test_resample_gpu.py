@@ -181,3 +181,22 @@ def test_resample_positions_past_32_bits():
     A = RNG.random((1, 2, 70001))
     out, ref = _resample(A, 5, 70001)
     parity.compare(out, ref, "f32")
+
+
+@pytest.mark.parametrize("dtype", [torch.uint8, torch.float16])
+def test_cascade_zoom_matches_oracle(dtype):
+    """2^k zoom by successive 2x levels (Sec. 3.3, Eq. zoomfactor), h halving
+    per level, FP32 intermediates carrying the input type's bound (direct
+    weights): against the oracle applied level by level to the FP32 values
+    each level stores; one FP32 tolerance per level."""
+    img = scenes.pixel_art(40, 56, seed=scenes.seed_for(6, 7))
+    A = scenes.planar(img).astype(np.float64) / 255.0
+    x = parity.encode(A, "u8" if dtype == torch.uint8 else "f16").to(DEV)
+    out = api.cascade_zoom(x, 3, out_dtype=torch.float32)
+    torch.cuda.synchronize()
+    cur = parity.decode(x.cpu())
+    for lvl in range(3):
+        cur = oracle.zoom2x(cur, h=1.0 / (1 << lvl)).astype(np.float32).astype(np.float64)
+    g = out.cpu().double().numpy()
+    assert g.shape == cur.shape == (3, 320, 448)
+    assert np.abs(g - cur).max() <= parity.F32_TOL * 3
