@@ -124,3 +124,19 @@ def test_batched_mixed_input_paths(dtype):
     torch.cuda.synchronize()
     for o, s in zip(outs, singles):
         assert torch.equal(o, s)
+
+
+def test_batched_fp32_with_data_bound():
+    """FP32 images with a caller's bound take the direct-weight batched
+    kernel; each equals the single-image kernel with the same parameters bit
+    for bit, and stays within FP32 rounding of the unbounded (scale-free)
+    result."""
+    imgs = _images(torch.float32, SIZES[:7], seed=13)
+    prm = api.Params(data_bound=1.0)
+    outs = api.zoom2x_batched(imgs, prm)
+    singles = [api.zoom2x_fwd(x, prm) for x in imgs]
+    plain = [api.zoom2x_fwd(x) for x in imgs]
+    torch.cuda.synchronize()
+    for o, s, q in zip(outs, singles, plain):
+        assert torch.equal(o, s)
+        assert (o - q).abs().max().item() <= 4e-6
