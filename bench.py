@@ -51,11 +51,11 @@ ALGO_MUFU_PER_PXCH = 15
 ALGO_BYTES_PER_PXCH = {"u8": 5, "f16": 10, "bf16": 10, "f32": 20}
 FP32_LANES_PER_SM = 128
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "zoom2x_fwd_1080p_u8.md")
+# The forward kernel's code: its tile body, device helpers and kernel
+# template (the .cu files around them only choose which instantiation runs).
 KERNEL_SOURCES = ["paper_2312_00229_gb300/csrc/wd_fwd_tile.cuh",
                   "paper_2312_00229_gb300/csrc/wd_common.cuh",
-                  "paper_2312_00229_gb300/csrc/wd_fwd_kernels.cuh",
-                  "paper_2312_00229_gb300/csrc/wd_fwd_typed.cu",
-                  "paper_2312_00229_gb300/csrc/wd_fwd.cu"]
+                  "paper_2312_00229_gb300/csrc/wd_fwd_kernels.cuh"]
 
 
 def parse_args():
@@ -538,10 +538,13 @@ def extras(torch, np, api, scenes, dev, world, hbm_peak):
     # 8x cascade of a 512x512 pixel-art image (three 2x passes, FP32 between)
     pa = torch.from_numpy(scenes.planar(scenes.pixel_art(512, 512, scenes.seed_for(4, 1)))).to(dev)
     t8, _ = time_graph(torch, [lambda: api.cascade_zoom(pa, 3)], 20)
+    t8f, _ = time_graph(torch, [lambda: api.cascade_zoom(pa, 3, fused=True)], 20)
     out["cascade8x"] = {"gpix_s": round(world * 4096 * 4096 / t8 / 1e9, 4),
                         "us": round(t8 * 1e6, 1),
+                        "fused_us": round(t8f * 1e6, 1),
                         "workload": "512x512x3 uint8 pixel art -> 4096x4096x3 uint8, "
-                                    "FP32 intermediates"}
+                                    "FP32 intermediates; us = one launch per level, fused_us "
+                                    "= all levels in one persistent launch"}
     del pa
     torch.cuda.empty_cache()
 

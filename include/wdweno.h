@@ -200,6 +200,38 @@ int weno_wait_timeouts(unsigned int* count, int reset);
 int weno_resample(const weno_image* in, weno_dtype in_t, const weno_image* out,
                   weno_dtype out_t, const weno_params* p, void* stream);
 
+/* 2^levels zoom by `levels` successive 2x zooms (Sec. 3.3, Eq. zoomfactor)
+ * in ONE persistent launch (plus a small setup kernel).  Level L zooms the
+ * image of level L-1 with h = p->h / 2^L (its coarse grid is the previous
+ * level's fine grid) and p->out_mode at every level; the intermediate images
+ * are FP32 planes in the workspace, and only the last level encodes to out_t.
+ * The result equals `levels` weno_zoom2x_fwd calls with FP32 intermediates.
+ * The input type's bound (uint8, FP16) or p->data_bound is carried to the
+ * later levels at 1.5625x per level, as weno_params.data_bound describes.
+ *   in, in_t   : n x m x C image
+ *   out, out_t : the last level's image: 2^L n x 2^L m in WENO_OUT_2N mode,
+ *                (2^L (n-1) + 1) x (2^L (m-1) + 1) in WENO_OUT_2N_MINUS_1
+ *   levels     : 1 .. WENO_CASCADE_MAX_LEVELS
+ *   workspace  : device scratch of >= weno_zoom2x_cascade_workspace_bytes
+ *                bytes, 256-byte aligned, overlapping neither image; no
+ *                initialisation needed; calls that share it must not overlap
+ * A tile of a later level waits (bounded, one second) for the bands of the
+ * previous level it reads; a wait that gives up is counted by
+ * weno_wait_timeouts.
+ * Returns WENO_OK, WENO_EINVAL (shapes, overlap, levels, parameters),
+ * WENO_EDTYPE, WENO_EWORKSPACE, WENO_ERANGE (more than 65535 bands in a
+ * level) or WENO_ECUDA. */
+#define WENO_CASCADE_MAX_LEVELS 6
+int weno_zoom2x_cascade(const weno_image* in, weno_dtype in_t, const weno_image* out,
+                        weno_dtype out_t, int levels, const weno_params* p, void* workspace,
+                        size_t workspace_bytes, void* stream);
+
+/* Scratch bytes of weno_zoom2x_cascade for `in`, `levels` and p's out_mode
+ * on the current device (the band heights follow its SM count); 0 for a
+ * malformed request. */
+size_t weno_zoom2x_cascade_workspace_bytes(const weno_image* in, int levels,
+                                           const weno_params* p);
+
 /* weno_zoom2x_batched without a workspace, for callers that cannot allocate
  * device memory (for example code inside another application's real-time
  * video pipeline, where cudaMalloc may synchronise the device and stall every

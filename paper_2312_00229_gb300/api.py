@@ -198,14 +198,44 @@ def _level_bounds(x: torch.Tensor, params: Params, levels: int):
 
 
 def cascade_zoom(x: torch.Tensor, levels: int, params: Optional[Params] = None, out_dtype=None,
-                 inter_dtype=torch.float32, layout: str = "chw") -> torch.Tensor:
+                 inter_dtype=torch.float32, layout: str = "chw",
+                 fused: bool = False) -> torch.Tensor:
     """``levels`` successive 2x zooms (Sec. 3.3, Eq. zoomfactor); the
     intermediate images are kept in ``inter_dtype`` and only the last one is
     encoded to ``out_dtype``.  Each level's coarse grid is the previous
     level's fine grid, so its spacing ``h`` is half the previous one.  The
     bound the input's type gives is carried to the later levels
-    (``data_bound``), so FP32 intermediates keep the direct weights."""
+    (``data_bound``), so FP32 intermediates keep the direct weights.
+
+    ``fused=True`` runs every level in one persistent launch
+    (``weno_zoom2x_cascade``; FP32 intermediates in a workspace) with the
+    same result."""
     params = params or Params()
+    if fused:
+        if inter_dtype != torch.float32:
+            raise ValueError("the fused cascade keeps FP32 intermediates")
+        _require_cuda(x, "x")
+        n, m = _hw(x, layout)
+        d = 1 if params.out_mode == B.WENO_OUT_2N_MINUS_1 else 0
+        oh, ow = n, m
+        for _ in range(levels):
+            oh, ow = 2 * oh - d, 2 * ow - d
+        shape = list(x.shape)
+        if layout == "hwc":
+            shape[0], shape[1] = oh, ow
+        else:
+            shape[-2], shape[-1] = oh, ow
+        out = torch.empty(shape, dtype=out_dtype or x.dtype, device=x.device)
+        xi, oi, pc = image(x, layout), image(out, layout), params.c()
+        nbytes = B.weno_zoom2x_cascade_workspace_bytes(xi, levels, pc)
+        if nbytes == 0:
+            raise ValueError("malformed cascade request")
+        ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=x.device)
+        base = (ws.data_ptr() + 255) & ~255
+        B.check("weno_zoom2x_cascade",
+                B.weno_zoom2x_cascade(xi, _DT[x.dtype], oi, _DT[out.dtype], levels, pc, base,
+                                      nbytes, _stream(x.device)))
+        return out
     bounds = _level_bounds(x, params, levels)
     cur = x
     for lvl in range(levels):

@@ -29,9 +29,12 @@ EXPORTS = (
     "weno_zoom2x_batched",
     "weno_zoom2x_batched_noalloc",
     "weno_resample",
+    "weno_zoom2x_cascade",
+    "weno_zoom2x_cascade_workspace_bytes",
     "weno_wait_timeouts",
 )
 WENO_NOALLOC_MAX_IMAGES = 4096
+WENO_CASCADE_MAX_LEVELS = 6
 
 
 class weno_params(ctypes.Structure):
@@ -78,6 +81,9 @@ _SIGS = {
                                      ctypes.c_int, ctypes.c_int, _VP], ctypes.c_int),
     "weno_resample": ([_IMG, ctypes.c_int, _IMG, ctypes.c_int, _PRM, _VP], ctypes.c_int),
     "weno_wait_timeouts": ([ctypes.POINTER(ctypes.c_uint), ctypes.c_int], ctypes.c_int),
+    "weno_zoom2x_cascade": ([_IMG, ctypes.c_int, _IMG, ctypes.c_int, ctypes.c_int, _PRM, _VP,
+                             ctypes.c_size_t, _VP], ctypes.c_int),
+    "weno_zoom2x_cascade_workspace_bytes": ([_IMG, ctypes.c_int, _PRM], ctypes.c_size_t),
 }
 
 _lock = threading.Lock()
@@ -170,6 +176,19 @@ def weno_zoom2x_batched_noalloc(count, d_in, in_t, d_out, out_t, params, rows_pe
 def weno_resample(inp, in_t, out, out_t, params, stream) -> int:
     return load().weno_resample(ctypes.byref(inp), in_t, ctypes.byref(out), out_t,
                                 ctypes.byref(params) if params is not None else None, stream)
+
+
+def weno_zoom2x_cascade(inp, in_t, out, out_t, levels, params, workspace, workspace_bytes,
+                        stream) -> int:
+    return load().weno_zoom2x_cascade(ctypes.byref(inp), in_t, ctypes.byref(out), out_t,
+                                      int(levels),
+                                      ctypes.byref(params) if params is not None else None,
+                                      workspace, int(workspace_bytes), stream)
+
+
+def weno_zoom2x_cascade_workspace_bytes(inp, levels, params) -> int:
+    return load().weno_zoom2x_cascade_workspace_bytes(
+        ctypes.byref(inp), int(levels), ctypes.byref(params) if params is not None else None)
 
 
 def weno_wait_timeouts(reset: bool = False) -> int:

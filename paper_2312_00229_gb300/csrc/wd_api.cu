@@ -8,6 +8,7 @@
 
 #include "wd_bwd.h"
 #include "wd_batched.h"
+#include "wd_cascade.h"
 #include "wd_common.cuh"
 #include "wd_fwd.h"
 #include "wd_resample.h"
@@ -219,6 +220,50 @@ FwdArgs make_fwd_args(const weno_image* in, int in_t, const weno_image* out, int
   return a;
 }
 
+// Fused 2^k cascade (Sec. 3.3, Eq. zoomfactor).
+static_assert(CASCADE_MAX_LEVELS == WENO_CASCADE_MAX_LEVELS, "cascade level limit");
+// Shapes, band heights and workspace layout of a cascade; false when the
+// request is malformed.  Level L zooms image L (image 0 = the input, image
+// `levels` = the output); images 1 .. levels-1 are FP32 planes in the
+// workspace, then come the queue head and the finished-strip counters.
+struct CascadePlan {
+  int levels;
+  int64_t n[CASCADE_MAX_LEVELS + 1], m[CASCADE_MAX_LEVELS + 1];
+  int64_t rpb[CASCADE_MAX_LEVELS];
+  size_t img_off[CASCADE_MAX_LEVELS + 1];  // byte offset of FP32 image L (1 .. levels-1)
+  size_t head_off, done_off, bytes;
+  int64_t done_count;
+};
+
+bool cascade_plan(const weno_image* in, int levels, const weno_params& p, CascadePlan* c) {
+  if (!image_ok(in) || levels < 1 || levels > CASCADE_MAX_LEVELS) return false;
+  if (p.out_mode != WENO_OUT_2N && p.out_mode != WENO_OUT_2N_MINUS_1) return false;
+  const int64_t d = p.out_mode == WENO_OUT_2N_MINUS_1 ? 1 : 0;
+  c->levels = levels;
+  c->n[0] = in->height;
+  c->m[0] = in->width;
+  size_t off = 0;
+  for (int L = 0; L < levels; ++L) {
+    c->n[L + 1] = 2 * c->n[L] - d;
+    c->m[L + 1] = 2 * c->m[L] - d;
+    if (c->n[L + 1] < 1 || c->m[L + 1] < 1 || c->n[L + 1] >= (int64_t(1) << 31) ||
+        c->m[L + 1] >= (int64_t(1) << 31))
+      return false;
+    c->rpb[L] = default_rows_per_band(c->n[L], c->m[L], in->channels);
+  }
+  c->done_count = 0;
+  for (int L = 0; L < levels; ++L) {
+    c->img_off[L + 1] = off;
+    if (L + 1 < levels)
+      off += ((size_t)(c->n[L + 1] * c->m[L + 1] * in->channels) * 4 + 255) & ~size_t(255);
+    c->done_count += ((c->n[L] + c->rpb[L] - 1) / c->rpb[L]) * in->channels;
+  }
+  c->head_off = off;
+  c->done_off = off + 16;
+  c->bytes = (c->done_off + 4 * (size_t)c->done_count + 255) & ~size_t(255);
+  return true;
+}
+
 }  // namespace
 
 extern "C" {
@@ -350,6 +395,83 @@ int weno_zoom2x_batched(int count, const weno_image* d_in, weno_dtype in_t,
   a.rows_per_band = rows_per_tile > 0 ? rows_per_tile : kBatchedRowsPerBand;
   a.workspace = workspace;
   cudaError_t e = launch_zoom2x_batched(a, k, bmode, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? WENO_OK : WENO_ECUDA;
+}
+
+size_t weno_zoom2x_cascade_workspace_bytes(const weno_image* in, int levels,
+                                           const weno_params* pp) {
+  const weno_params p = pp ? *pp : weno_params_default();
+  CascadePlan c;
+  return cascade_plan(in, levels, p, &c) ? c.bytes : 0;
+}
+
+int weno_zoom2x_cascade(const weno_image* in, weno_dtype in_t, const weno_image* out,
+                        weno_dtype out_t, int levels, const weno_params* pp, void* workspace,
+                        size_t workspace_bytes, void* stream) {
+  const weno_params p = pp ? *pp : weno_params_default();
+  if (!image_ok(in) || !image_ok(out)) return WENO_EINVAL;
+  if (dtype_size(in_t) == 0 || dtype_size(out_t) == 0) return WENO_EDTYPE;
+  CascadePlan c;
+  if (!cascade_plan(in, levels, p, &c)) return WENO_EINVAL;
+  if (out->height != c.n[levels] || out->width != c.m[levels] || out->channels != in->channels)
+    return WENO_EINVAL;
+  if (overlaps(in, dtype_size(in_t), out, dtype_size(out_t))) return WENO_EINVAL;
+  if (!workspace || workspace_bytes < c.bytes || reinterpret_cast<uintptr_t>(workspace) % 256)
+    return WENO_EWORKSPACE;
+  {  // the workspace overlaps neither image
+    weno_image w{workspace, 1, (int64_t)c.bytes, 1, (int64_t)c.bytes, (int64_t)c.bytes, 1};
+    if (overlaps(&w, 1, in, dtype_size(in_t)) || overlaps(&w, 1, out, dtype_size(out_t)))
+      return WENO_EINVAL;
+  }
+  for (int L = 0; L < levels; ++L)
+    if ((c.n[L] + c.rpb[L] - 1) / c.rpb[L] > 65535) return WENO_ERANGE;
+  unsigned char* ws = static_cast<unsigned char*>(workspace);
+  CascadeArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.levels = levels;
+  // one weight form for every level: the direct one when the input's bound,
+  // carried at 1.5625x (x values are convex combinations of interpolants with
+  // |p| <= 1.25 max|node|, "+" values take x values as nodes) with slack for
+  // the weights' rounding, proves the range at every level
+  int bmode = B2;
+  bool all_direct = true;
+  double bound = input_bound(p, in_t);
+  int64_t first = 0, done = 0;
+  for (int L = 0; L < levels; ++L) {
+    weno_params pl = p;
+    pl.h = float(double(p.h) / double(int64_t(1) << L));
+    pl.data_bound = float(bound);
+    int bm;
+    if (!fold_consts(pl, &a.k[L], &bm)) return WENO_EINVAL;
+    bmode = bm;
+    if (!(bound > 0.0) || !direct_b2_ok(pl, L == 0 ? int(in_t) : int(WENO_F32)))
+      all_direct = false;
+    bound *= 1.5625 * (1.0 + 1e-3);
+    weno_image src = *in, dst = *out;
+    if (L > 0) {
+      src = weno_image{ws + c.img_off[L], c.n[L], c.m[L], in->channels, c.n[L] * c.m[L], c.m[L], 1};
+    }
+    if (L + 1 < levels) {
+      dst = weno_image{ws + c.img_off[L + 1], c.n[L + 1], c.m[L + 1], in->channels,
+                       c.n[L + 1] * c.m[L + 1], c.m[L + 1], 1};
+    }
+    const int st = L == 0 ? int(in_t) : int(WENO_F32);
+    const int dt = L + 1 == levels ? int(out_t) : int(WENO_F32);
+    a.f[L] = make_fwd_args(&src, st, &dst, dt, c.n[L + 1], c.m[L + 1], c.rpb[L]);
+    a.f[L].in_bulk = 0;
+    a.strips[L] = (c.m[L] + tile_width_fwd() - 1) / tile_width_fwd();
+    a.bands[L] = (c.n[L] + c.rpb[L] - 1) / c.rpb[L];
+    a.first[L] = first;
+    first += a.strips[L] * a.bands[L] * in->channels;
+    a.done_off[L] = done;
+    done += a.bands[L] * in->channels;
+  }
+  a.first[levels] = first;
+  if (bmode == B2 && all_direct) bmode = B2R;
+  a.head = reinterpret_cast<unsigned long long*>(ws + c.head_off);
+  a.done = reinterpret_cast<unsigned int*>(ws + c.done_off);
+  a.done_count = c.done_count;
+  cudaError_t e = launch_zoom2x_cascade(a, bmode, in_t, out_t, static_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? WENO_OK : WENO_ECUDA;
 }
 

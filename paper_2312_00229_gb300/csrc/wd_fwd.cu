@@ -2,6 +2,7 @@
 // planes, one CTA per tile.  The tile body is in wd_fwd_tile.cuh.  Storage
 // types are compile-time parameters for the common pairs (wd_fwd_typed.cu);
 // any other pair, and beta != 2, goes through the run-time-typed kernels here.
+#include "wd_cascade.h"
 #include "wd_fwd_kernels.cuh"
 
 namespace wdweno {
@@ -27,11 +28,12 @@ cudaError_t launch_zoom2x_fwd(const FwdArgs& a, const MethodConsts& k, int bmode
 }
 
 cudaError_t fwd_wait_timeouts(unsigned int* count, bool reset) {
-  unsigned int a = 0, b = 0, c = 0;
+  unsigned int a = 0, b = 0, c = 0, d = 0;
   cudaError_t e = fwd_tile::read_wait_timeouts(&a, reset);
   if (e == cudaSuccess) e = fwd_wait_timeouts_typed(&b, reset);
   if (e == cudaSuccess) e = fwd_wait_timeouts_batched(&c, reset);
-  *count = a + b + c;
+  if (e == cudaSuccess) e = fwd_wait_timeouts_cascade(&d, reset);
+  *count = a + b + c + d;
   return e;
 }
 
