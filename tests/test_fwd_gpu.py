@@ -168,12 +168,13 @@ def test_fwd_4k_precision_sweep_sampled():
         _check_windows(parity.decode(x.cpu()), out, dt, api.Params(), wins)
 
 
-def test_fwd_large_planes_64bit_offsets():
-    """3 x 16384 x 16384 uint8 input: output offsets exceed 2^31."""
-    n = 16384
-    x = torch.empty(3, n, n, dtype=torch.uint8, device=DEV)
+@pytest.mark.parametrize("n,m", [(16384, 16384), (16000, 16001)])
+def test_fwd_large_planes_64bit_offsets(n, m):
+    """3 x n x m uint8 input: output offsets exceed 2^31; the odd width puts
+    the rows at every 16-byte alignment (bulk copies of any row start)."""
+    x = torch.empty(3, n, m, dtype=torch.uint8, device=DEV)
     g = torch.Generator(device=DEV).manual_seed(7)
-    x.copy_(torch.randint(0, 256, (3, n, n), device=DEV, generator=g, dtype=torch.uint8))
+    x.copy_(torch.randint(0, 256, (3, n, m), device=DEV, generator=g, dtype=torch.uint8))
     out = api.zoom2x_fwd(x)
     torch.cuda.synchronize()
     A01 = x[:, -40:, -60:].cpu().numpy().astype(np.float64) / 255.0
