@@ -66,12 +66,16 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--skip-extras", action="store_true",
                     help="headline only (no fwd+bwd / batched / sweep / cascade)")
-    ap.add_argument("--case", choices=["headline", "resample3x", "fwdbwd", "batched"],
+    ap.add_argument("--case", choices=["headline", "resample3x", "fwdbwd", "batched",
+                                       "cascade8x"],
                     default="headline",
                     help="run one secondary workload alone (for profiling) instead of the "
                          "headline line: resample3x = 1920x1080x3 uint8 -> 5760x3240 tensor "
                          "WENO; fwdbwd = one autograd step on Bx3x512x512 FP32; batched = "
-                         "one persistent launch over B uneven FP16 RGB images")
+                         "one persistent launch over B uneven FP16 RGB images; cascade8x = "
+                         "512x512x3 uint8 pixel art zoomed 8x by three 2x levels")
+    ap.add_argument("--fused", action="store_true",
+                    help="--case cascade8x: all levels in one persistent launch")
     ap.add_argument("--batch", type=int, default=None,
                     help="images per step of --case fwdbwd (default 32, the workload) or "
                          "--case batched (default 256, the workload)")
@@ -614,6 +618,12 @@ def run_case(args):
         o = torch.empty(3, 3240, 5760, dtype=torch.uint8, device=dev)
         step = lambda: api.resample(hd, 3240, 5760, out=o)
         work = "1920x1080x3 uint8 -> 5760x3240x3 uint8, tensor WENO"
+    elif args.case == "cascade8x":
+        pa = torch.from_numpy(scenes.planar(scenes.pixel_art(512, 512, scenes.seed_for(4, 1))))
+        pa = pa.to(dev)
+        step = lambda: api.cascade_zoom(pa, 3, fused=args.fused)
+        work = ("512x512x3 uint8 pixel art -> 4096x4096x3 uint8, FP32 intermediates, " +
+                ("one persistent launch" if args.fused else "one launch per level"))
     elif args.case == "batched":
         count = args.batch or 256
         xs = [torch.from_numpy(scenes.planar(im)).to(dev).float().div(255).half()
