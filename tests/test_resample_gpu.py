@@ -200,3 +200,17 @@ def test_cascade_zoom_matches_oracle(dtype):
     g = out.cpu().double().numpy()
     assert g.shape == cur.shape == (3, 320, 448)
     assert np.abs(g - cur).max() <= parity.F32_TOL * 3
+
+
+def test_resample_fp32_with_data_bound():
+    """FP32 input with a caller's bound takes the direct weights: oracle
+    parity, and agreement with the scaled weights (no bound) to a few FP32
+    rounding steps."""
+    A = RNG.random((2, 45, 70))
+    out, ref = _resample(A, 130, 201, params=api.Params(data_bound=1.0))
+    parity.compare(out, ref, "f32")
+    x = torch.from_numpy(A.astype(np.float32)).to(DEV)
+    a = api.resample(x, 130, 201, api.Params(data_bound=1.0))
+    b = api.resample(x, 130, 201)
+    torch.cuda.synchronize()
+    assert (a - b).abs().max().item() <= 4e-6
