@@ -35,6 +35,13 @@ namespace wdweno {
 namespace {
 
 constexpr int G = BWD_GHOST;
+// A 32 x 8 block covers 32 columns and R x 8 rows of cells: a thread takes R
+// cells of its column, 8 rows apart.  The light kernels take several cells, so
+// a block's start-up is spread over more work; the heavy ones take one, which
+// keeps their register count (and occupancy) down.
+constexpr int BWD_BY = 8;
+constexpr int R_XSI = 4, R_XVAL = 4, R_PSI = 4, R_PADJ = 1, R_COEF2 = 1, R_G2 = 1, R_COEF1 = 1,
+              R_G1 = 4, R_FOLD = 4;
 
 // Workspace layout per plane (NE x ME cells, the cell count padded to a
 // multiple of 4): seven float4 planes for the four-direction vectors, then
@@ -215,7 +222,10 @@ __device__ __forceinline__ void point_adjoint(const Pt& q, const float D[4], flo
   }
 }
 
-__device__ __forceinline__ bool setup(const BwdArgs& a, const MethodConsts& k, Ctx& c, int& I,
+// The thread's column J and first row I0; it takes rows I0 + r BWD_BY,
+// r < R, that lie on the extended grid.
+template <int R>
+__device__ __forceinline__ bool setup(const BwdArgs& a, const MethodConsts& k, Ctx& c, int& I0,
                                       int& J) {
   const int64_t plane = blockIdx.z;
   c.n = (int)a.n; c.m = (int)a.m; c.sh = a.x_sh; c.sw = a.x_sw;
@@ -226,8 +236,8 @@ __device__ __forceinline__ bool setup(const BwdArgs& a, const MethodConsts& k, C
   c.w = k.w; c.kap1 = k.kappa1; c.kap2 = k.kappa2; c.eps1 = k.eps1; c.eps2 = k.eps2;
   c.beta = k.beta;
   J = (int)(blockIdx.x * blockDim.x + threadIdx.x) - G;
-  I = (int)(blockIdx.y * blockDim.y + threadIdx.y) - G;
-  return I < c.n + G && J < c.m + G;
+  I0 = (int)(blockIdx.y * (BWD_BY * R) + threadIdx.y) - G;
+  return J < c.m + G;
 }
 
 __device__ __forceinline__ float gout_at(const BwdArgs& a, int64_t plane, int64_t P, int64_t Q) {
@@ -244,16 +254,20 @@ __device__ __forceinline__ bool in_core(const Ctx& c, int I, int J) {
 
 // ---- forward recompute ------------------------------------------------------
 __global__ void k_xsi(BwdArgs a, MethodConsts k) {
-  Ctx c; int I, J;
-  if (!setup(a, k, c, I, J)) return;
-  float si[4] = {0.f, 0.f, 0.f, 0.f};
-  if (in_core(c, I, J)) {
-    const Pt q = eval_pt<false>(c, 0, I, J);
-#pragma unroll
-    for (int d = 0; d < 4; ++d) si[d] = q.si[d];
+  Ctx c; int I0, J;
+  if (!setup<R_XSI>(a, k, c, I0, J)) return;
+  for (int r = 0; r < R_XSI; ++r) {
+    const int I = I0 + r * BWD_BY;
+    if (I >= c.n + G) break;
+    float si[4] = {0.f, 0.f, 0.f, 0.f};
+    if (in_core(c, I, J)) {
+      const Pt q = eval_pt<false>(c, 0, I, J);
+  #pragma unroll
+      for (int d = 0; d < 4; ++d) si[d] = q.si[d];
+    }
+    V(c, G_XSI, I, J) = f4(si);
+    W(c, S_A, I, J) = Ahat(c, I, J);
   }
-  V(c, G_XSI, I, J) = f4(si);
-  W(c, S_A, I, J) = Ahat(c, I, J);
 }
 
 template <int BMODE>
@@ -267,73 +281,85 @@ __device__ __forceinline__ void d_x(const Ctx& c, int I, int J, const float si[4
 
 template <int BMODE>
 __global__ void k_xval(BwdArgs a, MethodConsts k) {
-  Ctx c; int I, J;
-  if (!setup(a, k, c, I, J)) return;
-  float v = 0.f;
-  if (I >= -4 && I < c.n + 4 && J >= -4 && J < c.m + 4) {
-    const Pt q = eval_pt(c, 0, I, J);
-    float D[4], om[4];
-    d_x<BMODE>(c, I, J, q.si, D);
-    weights<BMODE>(D, c.beta, om);
-    v = om[0] * q.p[0] + om[1] * q.p[1] + om[2] * q.p[2] + om[3] * q.p[3];
+  Ctx c; int I0, J;
+  if (!setup<R_XVAL>(a, k, c, I0, J)) return;
+  for (int r = 0; r < R_XVAL; ++r) {
+    const int I = I0 + r * BWD_BY;
+    if (I >= c.n + G) break;
+    float v = 0.f;
+    if (I >= -4 && I < c.n + 4 && J >= -4 && J < c.m + 4) {
+      const Pt q = eval_pt(c, 0, I, J);
+      float D[4], om[4];
+      d_x<BMODE>(c, I, J, q.si, D);
+      weights<BMODE>(D, c.beta, om);
+      v = om[0] * q.p[0] + om[1] * q.p[1] + om[2] * q.p[2] + om[3] * q.p[3];
+    }
+    W(c, S_X, I, J) = v;
   }
-  W(c, S_X, I, J) = v;
 }
 
 __global__ void k_psi(BwdArgs a, MethodConsts k) {
-  Ctx c; int I, J;
-  if (!setup(a, k, c, I, J)) return;
-  float e[4] = {0.f, 0.f, 0.f, 0.f}, s[4] = {0.f, 0.f, 0.f, 0.f};
-  if (I >= -2 && I < c.n + 2 && J >= -2 && J < c.m + 2) {
-    const Pt qe = eval_pt(c, 1, I, J);
-    const Pt qs = eval_pt(c, 2, I, J);
-#pragma unroll
-    for (int d = 0; d < 4; ++d) { e[d] = qe.si[d]; s[d] = qs.si[d]; }
+  Ctx c; int I0, J;
+  if (!setup<R_PSI>(a, k, c, I0, J)) return;
+  for (int r = 0; r < R_PSI; ++r) {
+    const int I = I0 + r * BWD_BY;
+    if (I >= c.n + G) break;
+    float e[4] = {0.f, 0.f, 0.f, 0.f}, s[4] = {0.f, 0.f, 0.f, 0.f};
+    if (I >= -2 && I < c.n + 2 && J >= -2 && J < c.m + 2) {
+      const Pt qe = eval_pt(c, 1, I, J);
+      const Pt qs = eval_pt(c, 2, I, J);
+  #pragma unroll
+      for (int d = 0; d < 4; ++d) { e[d] = qe.si[d]; s[d] = qs.si[d]; }
+    }
+    V(c, G_ESI, I, J) = f4(e);
+    V(c, G_SSI, I, J) = f4(s);
   }
-  V(c, G_ESI, I, J) = f4(e);
-  V(c, G_SSI, I, J) = f4(s);
 }
 
 // ---- phase-2 adjoint ------------------------------------------------------------
 template <int BMODE>
 __global__ void k_padj(BwdArgs a, MethodConsts k) {
-  Ctx c; int I, J;
-  if (!setup(a, k, c, I, J)) return;
-  float pE[4] = {0.f, 0.f, 0.f, 0.f}, dE[4] = {0.f, 0.f, 0.f, 0.f};
-  float pS[4] = {0.f, 0.f, 0.f, 0.f}, dS[4] = {0.f, 0.f, 0.f, 0.f};
-  if (I >= 0 && I < c.n && J >= 0 && J < c.m) {
-    const int64_t plane = blockIdx.z;
-    const float uE = gout_at(a, plane, 2 * (int64_t)I, 2 * (int64_t)J + 1);
-    const float uS = gout_at(a, plane, 2 * (int64_t)I + 1, 2 * (int64_t)J);
-    if (uE != 0.f) {
-      // E(a,b): D reads S at (a-1,b), (a,b), (a-1,b+1), (a,b+1)
-      const Pt q = eval_pt(c, 1, I, J);
-      float D[4];
-      const float4 n0 = V(c, G_SSI, I - 1, J), n1 = V(c, G_SSI, I, J);
-      const float4 n2 = V(c, G_SSI, I - 1, J + 1), n3 = V(c, G_SSI, I, J + 1);
-      const float4 own = V(c, G_ESI, I, J);
-#pragma unroll
-      for (int d = 0; d < 4; ++d)
-        D[d] = fmaf(c.w, comp(n0, d) + comp(n1, d) + comp(n2, d) + comp(n3, d), comp(own, d));
-      point_adjoint<BMODE>(q, D, c.beta, uE, pE, dE);
+  Ctx c; int I0, J;
+  if (!setup<R_PADJ>(a, k, c, I0, J)) return;
+  for (int r = 0; r < R_PADJ; ++r) {
+    const int I = I0 + r * BWD_BY;
+    if (I >= c.n + G) break;
+    float pE[4] = {0.f, 0.f, 0.f, 0.f}, dE[4] = {0.f, 0.f, 0.f, 0.f};
+    float pS[4] = {0.f, 0.f, 0.f, 0.f}, dS[4] = {0.f, 0.f, 0.f, 0.f};
+    if (I >= 0 && I < c.n && J >= 0 && J < c.m) {
+      const int64_t plane = blockIdx.z;
+      const float uE = gout_at(a, plane, 2 * (int64_t)I, 2 * (int64_t)J + 1);
+      const float uS = gout_at(a, plane, 2 * (int64_t)I + 1, 2 * (int64_t)J);
+      if (uE != 0.f) {
+        // E(a,b): D reads S at (a-1,b), (a,b), (a-1,b+1), (a,b+1)
+        const Pt q = eval_pt(c, 1, I, J);
+        float D[4];
+        const float4 n0 = V(c, G_SSI, I - 1, J), n1 = V(c, G_SSI, I, J);
+        const float4 n2 = V(c, G_SSI, I - 1, J + 1), n3 = V(c, G_SSI, I, J + 1);
+        const float4 own = V(c, G_ESI, I, J);
+  #pragma unroll
+        for (int d = 0; d < 4; ++d)
+          D[d] = fmaf(c.w, comp(n0, d) + comp(n1, d) + comp(n2, d) + comp(n3, d), comp(own, d));
+        point_adjoint<BMODE>(q, D, c.beta, uE, pE, dE);
+      }
+      if (uS != 0.f) {
+        // S(a,b): D reads E at (a,b-1), (a,b), (a+1,b-1), (a+1,b)
+        const Pt q = eval_pt(c, 2, I, J);
+        float D[4];
+        const float4 n0 = V(c, G_ESI, I, J - 1), n1 = V(c, G_ESI, I, J);
+        const float4 n2 = V(c, G_ESI, I + 1, J - 1), n3 = V(c, G_ESI, I + 1, J);
+        const float4 own = V(c, G_SSI, I, J);
+  #pragma unroll
+        for (int d = 0; d < 4; ++d)
+          D[d] = fmaf(c.w, comp(n0, d) + comp(n1, d) + comp(n2, d) + comp(n3, d), comp(own, d));
+        point_adjoint<BMODE>(q, D, c.beta, uS, pS, dS);
+      }
     }
-    if (uS != 0.f) {
-      // S(a,b): D reads E at (a,b-1), (a,b), (a+1,b-1), (a+1,b)
-      const Pt q = eval_pt(c, 2, I, J);
-      float D[4];
-      const float4 n0 = V(c, G_ESI, I, J - 1), n1 = V(c, G_ESI, I, J);
-      const float4 n2 = V(c, G_ESI, I + 1, J - 1), n3 = V(c, G_ESI, I + 1, J);
-      const float4 own = V(c, G_SSI, I, J);
-#pragma unroll
-      for (int d = 0; d < 4; ++d)
-        D[d] = fmaf(c.w, comp(n0, d) + comp(n1, d) + comp(n2, d) + comp(n3, d), comp(own, d));
-      point_adjoint<BMODE>(q, D, c.beta, uS, pS, dS);
-    }
+    V(c, G_EP, I, J) = f4(pE);
+    V(c, G_ED, I, J) = f4(dE);
+    V(c, G_SP, I, J) = f4(pS);
+    V(c, G_SD, I, J) = f4(dS);
   }
-  V(c, G_EP, I, J) = f4(pE);
-  V(c, G_ED, I, J) = f4(dE);
-  V(c, G_SP, I, J) = f4(pS);
-  V(c, G_SD, I, J) = f4(dS);
 }
 
 // SI_bar of the four directions at a point: its own D_bar plus w times the
@@ -390,23 +416,27 @@ __device__ __forceinline__ void coef_point(const Ctx& c, int type, int I, int J,
 }
 
 __global__ void k_coef2(BwdArgs a, MethodConsts k) {
-  Ctx c; int I, J;
-  if (!setup(a, k, c, I, J)) return;
-  // E points whose adjoint can be nonzero: rows 0..n, columns -1..m-1;
-  // S points: rows -1..n-1, columns 0..m.  Elsewhere the coefficients are 0.
-  const bool e_live = I >= 0 && I <= c.n && J >= -1 && J < c.m;
-  const bool s_live = I >= -1 && I < c.n && J >= 0 && J <= c.m;
-  if (e_live) {
-    coef_point(c, 1, I, J, G_EP, 0, G_ED, G_SD, S_ECO);
-  } else {
-#pragma unroll
-    for (int q = 0; q < 12; ++q) W(c, S_ECO + q, I, J) = 0.f;
-  }
-  if (s_live) {
-    coef_point(c, 2, I, J, G_SP, 0, G_ED, G_SD, S_SCO);
-  } else {
-#pragma unroll
-    for (int q = 0; q < 12; ++q) W(c, S_SCO + q, I, J) = 0.f;
+  Ctx c; int I0, J;
+  if (!setup<R_COEF2>(a, k, c, I0, J)) return;
+  for (int r = 0; r < R_COEF2; ++r) {
+    const int I = I0 + r * BWD_BY;
+    if (I >= c.n + G) break;
+    // E points whose adjoint can be nonzero: rows 0..n, columns -1..m-1;
+    // S points: rows -1..n-1, columns 0..m.  Elsewhere the coefficients are 0.
+    const bool e_live = I >= 0 && I <= c.n && J >= -1 && J < c.m;
+    const bool s_live = I >= -1 && I < c.n && J >= 0 && J <= c.m;
+    if (e_live) {
+      coef_point(c, 1, I, J, G_EP, 0, G_ED, G_SD, S_ECO);
+    } else {
+  #pragma unroll
+      for (int q = 0; q < 12; ++q) W(c, S_ECO + q, I, J) = 0.f;
+    }
+    if (s_live) {
+      coef_point(c, 2, I, J, G_SP, 0, G_ED, G_SD, S_SCO);
+    } else {
+  #pragma unroll
+      for (int q = 0; q < 12; ++q) W(c, S_SCO + q, I, J) = 0.f;
+    }
   }
 }
 
@@ -430,73 +460,91 @@ __device__ __forceinline__ float gather(const Ctx& c, int type, int lattice, int
 // kernel reads them).
 template <int BMODE>
 __global__ void k_gather2_xadj(BwdArgs a, MethodConsts k) {
-  Ctx c; int I, J;
-  if (!setup(a, k, c, I, J)) return;
-  const int64_t plane = blockIdx.z;
-  float xb = gather(c, 1, 1, I, J, S_ECO) + gather(c, 2, 1, I, J, S_SCO);
-  float ab = gather(c, 1, 0, I, J, S_ECO) + gather(c, 2, 0, I, J, S_SCO);
-  if (I >= 0 && I < c.n && J >= 0 && J < c.m) {
-    xb += gout_at(a, plane, 2 * (int64_t)I + 1, 2 * (int64_t)J + 1);
-    ab += gout_at(a, plane, 2 * (int64_t)I, 2 * (int64_t)J);
+  Ctx c; int I0, J;
+  if (!setup<R_G2>(a, k, c, I0, J)) return;
+  for (int r = 0; r < R_G2; ++r) {
+    const int I = I0 + r * BWD_BY;
+    if (I >= c.n + G) break;
+    const int64_t plane = blockIdx.z;
+    float xb = gather(c, 1, 1, I, J, S_ECO) + gather(c, 2, 1, I, J, S_SCO);
+    float ab = gather(c, 1, 0, I, J, S_ECO) + gather(c, 2, 0, I, J, S_SCO);
+    if (I >= 0 && I < c.n && J >= 0 && J < c.m) {
+      xb += gout_at(a, plane, 2 * (int64_t)I + 1, 2 * (int64_t)J + 1);
+      ab += gout_at(a, plane, 2 * (int64_t)I, 2 * (int64_t)J);
+    }
+    W(c, S_AB, I, J) = ab;
+    // ---- phase-1 adjoint of this x point ----
+    float pX[4] = {0.f, 0.f, 0.f, 0.f}, dX[4] = {0.f, 0.f, 0.f, 0.f};
+    if (xb != 0.f && I >= -4 && I < c.n + 4 && J >= -4 && J < c.m + 4) {
+      const Pt q = eval_pt(c, 0, I, J);
+      float D[4];
+      d_x<BMODE>(c, I, J, q.si, D);
+      point_adjoint<BMODE>(q, D, c.beta, xb, pX, dX);
+    }
+    V(c, G_EP, I, J) = f4(pX);
+    V(c, G_ED, I, J) = f4(dX);
   }
-  W(c, S_AB, I, J) = ab;
-  // ---- phase-1 adjoint of this x point ----
-  float pX[4] = {0.f, 0.f, 0.f, 0.f}, dX[4] = {0.f, 0.f, 0.f, 0.f};
-  if (xb != 0.f && I >= -4 && I < c.n + 4 && J >= -4 && J < c.m + 4) {
-    const Pt q = eval_pt(c, 0, I, J);
-    float D[4];
-    d_x<BMODE>(c, I, J, q.si, D);
-    point_adjoint<BMODE>(q, D, c.beta, xb, pX, dX);
-  }
-  V(c, G_EP, I, J) = f4(pX);
-  V(c, G_ED, I, J) = f4(dX);
 }
 
 __global__ void k_coef1(BwdArgs a, MethodConsts k) {
-  Ctx c; int I, J;
-  if (!setup(a, k, c, I, J)) return;
-  if (I >= -5 && I < c.n + 5 && J >= -5 && J < c.m + 5) {
-    coef_point(c, 0, I, J, G_EP, G_ED, 0, 0, S_ECO);
-  } else {
-#pragma unroll
-    for (int q = 0; q < 12; ++q) W(c, S_ECO + q, I, J) = 0.f;
+  Ctx c; int I0, J;
+  if (!setup<R_COEF1>(a, k, c, I0, J)) return;
+  for (int r = 0; r < R_COEF1; ++r) {
+    const int I = I0 + r * BWD_BY;
+    if (I >= c.n + G) break;
+    if (I >= -5 && I < c.n + 5 && J >= -5 && J < c.m + 5) {
+      coef_point(c, 0, I, J, G_EP, G_ED, 0, 0, S_ECO);
+    } else {
+  #pragma unroll
+      for (int q = 0; q < 12; ++q) W(c, S_ECO + q, I, J) = 0.f;
+    }
   }
 }
 
 __global__ void k_gather1(BwdArgs a, MethodConsts k) {
-  Ctx c; int I, J;
-  if (!setup(a, k, c, I, J)) return;
-  W(c, S_AB, I, J) += gather(c, 0, 0, I, J, S_ECO);
+  Ctx c; int I0, J;
+  if (!setup<R_G1>(a, k, c, I0, J)) return;
+  for (int r = 0; r < R_G1; ++r) {
+    const int I = I0 + r * BWD_BY;
+    if (I >= c.n + G) break;
+    W(c, S_AB, I, J) += gather(c, 0, 0, I, J, S_ECO);
+  }
 }
 
 // grad_in(i, j) = sum of A_bar over the extended cells that clamp to (i, j).
 __global__ void k_fold(BwdArgs a, MethodConsts k) {
-  Ctx c; int I, J;
-  if (!setup(a, k, c, I, J)) return;
-  if (I < 0 || I >= c.n || J < 0 || J >= c.m) return;
-  const int i0 = I == 0 ? -G : I, i1 = I == c.n - 1 ? c.n - 1 + G : I;
-  const int j0 = J == 0 ? -G : J, j1 = J == c.m - 1 ? c.m - 1 + G : J;
-  float acc = 0.f;
-  for (int ii = i0; ii <= i1; ++ii)
-    for (int jj = j0; jj <= j1; ++jj) acc += W(c, S_AB, ii, jj);
-  const int64_t plane = blockIdx.z;
-  a.gin[plane * a.gi_sc + (int64_t)I * a.gi_sh + (int64_t)J * a.gi_sw] = acc;
+  Ctx c; int I0, J;
+  if (!setup<R_FOLD>(a, k, c, I0, J)) return;
+  for (int r = 0; r < R_FOLD; ++r) {
+    const int I = I0 + r * BWD_BY;
+    if (I >= c.n + G) break;
+    if (I < 0 || I >= c.n || J < 0 || J >= c.m) continue;
+    const int i0 = I == 0 ? -G : I, i1 = I == c.n - 1 ? c.n - 1 + G : I;
+    const int j0 = J == 0 ? -G : J, j1 = J == c.m - 1 ? c.m - 1 + G : J;
+    float acc = 0.f;
+    for (int ii = i0; ii <= i1; ++ii)
+      for (int jj = j0; jj <= j1; ++jj) acc += W(c, S_AB, ii, jj);
+    const int64_t plane = blockIdx.z;
+    a.gin[plane * a.gi_sc + (int64_t)I * a.gi_sh + (int64_t)J * a.gi_sw] = acc;
+  }
 }
 
 template <int BMODE>
 cudaError_t launch_all(const BwdArgs& a, const MethodConsts& k, cudaStream_t st) {
-  const dim3 block(32, 8);
-  const dim3 grid((unsigned)((a.m + 2 * G + 31) / 32), (unsigned)((a.n + 2 * G + 7) / 8),
-                  (unsigned)a.planes);
-  k_xsi<<<grid, block, 0, st>>>(a, k);
-  k_xval<BMODE><<<grid, block, 0, st>>>(a, k);
-  k_psi<<<grid, block, 0, st>>>(a, k);
-  k_padj<BMODE><<<grid, block, 0, st>>>(a, k);
-  k_coef2<<<grid, block, 0, st>>>(a, k);
-  k_gather2_xadj<BMODE><<<grid, block, 0, st>>>(a, k);
-  k_coef1<<<grid, block, 0, st>>>(a, k);
-  k_gather1<<<grid, block, 0, st>>>(a, k);
-  k_fold<<<grid, block, 0, st>>>(a, k);
+  const dim3 block(32, BWD_BY);
+  auto grid = [&](int R) {
+    return dim3((unsigned)((a.m + 2 * G + 31) / 32),
+                (unsigned)((a.n + 2 * G + BWD_BY * R - 1) / (BWD_BY * R)), (unsigned)a.planes);
+  };
+  k_xsi<<<grid(R_XSI), block, 0, st>>>(a, k);
+  k_xval<BMODE><<<grid(R_XVAL), block, 0, st>>>(a, k);
+  k_psi<<<grid(R_PSI), block, 0, st>>>(a, k);
+  k_padj<BMODE><<<grid(R_PADJ), block, 0, st>>>(a, k);
+  k_coef2<<<grid(R_COEF2), block, 0, st>>>(a, k);
+  k_gather2_xadj<BMODE><<<grid(R_G2), block, 0, st>>>(a, k);
+  k_coef1<<<grid(R_COEF1), block, 0, st>>>(a, k);
+  k_gather1<<<grid(R_G1), block, 0, st>>>(a, k);
+  k_fold<<<grid(R_FOLD), block, 0, st>>>(a, k);
   return cudaGetLastError();
 }
 
