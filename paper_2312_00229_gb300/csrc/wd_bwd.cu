@@ -36,12 +36,12 @@ namespace {
 
 constexpr int G = BWD_GHOST;
 // A 32 x 8 block covers 32 columns and R x 8 rows of cells: a thread takes R
-// cells of its column, 8 rows apart.  The light kernels take several cells, so
-// a block's start-up is spread over more work; the heavy ones take one, which
-// keeps their register count (and occupancy) down.
+// cells of its column, 8 rows apart.  Three light kernels take four cells, so
+// a block's start-up is spread over more work; the others take one, which
+// keeps their register count (and occupancy) down (chosen by measurement).
 constexpr int BWD_BY = 8;
-constexpr int R_XSI = 4, R_XVAL = 4, R_PSI = 4, R_PADJ = 1, R_COEF2 = 1, R_G2 = 1, R_COEF1 = 1,
-              R_G1 = 4, R_FOLD = 4;
+constexpr int R_XSI = 4, R_XVAL = 4, R_PSI = 1, R_PADJ = 1, R_COEF2 = 1, R_G2 = 1, R_COEF1 = 1,
+              R_G1 = 1, R_FOLD = 4;
 
 // Workspace layout per plane (NE x ME cells, the cell count padded to a
 // multiple of 4): seven float4 planes for the four-direction vectors, then
