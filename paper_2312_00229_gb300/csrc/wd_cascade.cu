@@ -36,11 +36,14 @@ constexpr int SETUP_THREADS = 256;
 // input of other types through the read-only path.
 template <class TIn, class TOut>
 struct CascadeIO {
-  __device__ __forceinline__ static float load(const void* base, int64_t idx, int) {
+  __device__ __forceinline__ static uint32_t load_bits(const void* base, int64_t idx, int) {
     if constexpr (std::is_same<TIn, float>::value)
-      return __ldcg(static_cast<const float*>(base) + idx);
+      return __float_as_uint(__ldcg(static_cast<const float*>(base) + idx));
     else
-      return to_float(__ldg(static_cast<const TIn*>(base) + idx));
+      return load_elem_bits(base, idx, DTypeOf<TIn>::value);
+  }
+  __device__ __forceinline__ static float value(uint32_t b, int) {
+    return elem_bits_value(b, DTypeOf<TIn>::value);
   }
   __device__ __forceinline__ static int in_size(int) { return (int)sizeof(TIn); }
   __device__ __forceinline__ static float decode(const unsigned char* p, int) {
@@ -57,9 +60,12 @@ struct CascadeIO {
 
 // Any storage pair, types chosen at run time.
 struct CascadeDynIO {
-  __device__ __forceinline__ static float load(const void* base, int64_t idx, int dt) {
-    if (dt == DT_F32) return __ldcg(static_cast<const float*>(base) + idx);
-    return load_elem(base, idx, dt);
+  __device__ __forceinline__ static uint32_t load_bits(const void* base, int64_t idx, int dt) {
+    if (dt == DT_F32) return __float_as_uint(__ldcg(static_cast<const float*>(base) + idx));
+    return load_elem_bits(base, idx, dt);
+  }
+  __device__ __forceinline__ static float value(uint32_t b, int dt) {
+    return elem_bits_value(b, dt);
   }
   __device__ __forceinline__ static int in_size(int dt) {
     return dt == DT_U8 ? 1 : (dt == DT_F32 ? 4 : 2);

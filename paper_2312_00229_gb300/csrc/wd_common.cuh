@@ -144,6 +144,35 @@ __device__ __forceinline__ float load_elem(const void* base, int64_t idx, int dt
   }
 }
 
+// The storage bits of one element, zero-extended, and the value they hold.
+// A prefetched element is kept in its storage form until its value is used:
+// the conversion is then not where the load is issued, so nothing waits for
+// the load there.
+__device__ __forceinline__ uint32_t load_elem_bits(const void* base, int64_t idx, int dt) {
+  switch (dt) {
+    case DT_U8:
+      return __ldg(static_cast<const uint8_t*>(base) + idx);
+    case DT_F16:
+    case DT_BF16:
+      return __ldg(static_cast<const unsigned short*>(base) + idx);
+    default:
+      return __float_as_uint(__ldg(static_cast<const float*>(base) + idx));
+  }
+}
+
+__device__ __forceinline__ float elem_bits_value(uint32_t b, int dt) {
+  switch (dt) {
+    case DT_U8:
+      return (float)b * (1.0f / 255.0f);
+    case DT_F16:
+      return __half2float(__ushort_as_half((unsigned short)b));
+    case DT_BF16:
+      return __bfloat162float(__ushort_as_bfloat16((unsigned short)b));
+    default:
+      return __uint_as_float(b);
+  }
+}
+
 // saturate, scale, round half to even: adding 1.5 * 2^23 inside the FMA
 // leaves a float whose unit in the last place is 1, so its low mantissa byte
 // is the code, from one rounding of the exact product.

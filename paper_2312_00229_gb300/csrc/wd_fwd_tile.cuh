@@ -242,9 +242,10 @@ struct FwdTile {
       atomicAdd(&g_wait_timeouts, 1u);
   }
 
-  __device__ __forceinline__ float load_row(int r) const {
+  // Storage bits of input row r (clamped), column c.
+  __device__ __forceinline__ uint32_t load_row(int r) const {
     const int rc = r < 0 ? 0 : (r > n - 1 ? n - 1 : r);
-    return IO::load(in, in_idx + (int64_t)rc * in_sh, in_dtype);
+    return IO::load_bits(in, in_idx + (int64_t)rc * in_sh, in_dtype);
   }
 
   // Element index `base` (fine row, column 2c) and the next column.
@@ -273,7 +274,7 @@ struct FwdTile {
   // output: the guards are compiled out so the whole step is one block for
   // the scheduler.
   template <int PH, bool FULL>
-  __device__ __forceinline__ void step(int s, float& pf, float& pf2, Carry& C) {
+  __device__ __forceinline__ void step(int s, uint32_t& pf, uint32_t& pf2, Carry& C) {
     constexpr int Q = PH ^ 1;  // slot written by the previous step
     const int rs = s - a0;
     if (!FULL && rs > H + 6) return;  // padding step past the band (uniform)
@@ -281,9 +282,9 @@ struct FwdTile {
     oE += 2 * out_sh;
 
     const int j = rs + HALO_L;  // load number of row s (the sweep starts at a0 - 4)
-    float cur = 0.f;
+    uint32_t cur = 0u;
     if constexpr (INB == IN_REG) {
-      cur = pf;               // input row s, loaded in step s-2
+      cur = pf;               // input row s, loaded in step s-2 (storage bits)
       pf = pf2;
       pf2 = load_row(s + 2);  // prefetch two rows ahead
     }
@@ -298,7 +299,7 @@ struct FwdTile {
       // the slot of load j + KAHEAD was last decoded in step s-2
       if (t == 0 && rs >= -HALO_L && rs + KAHEAD <= H + 5) issue_row(j + KAHEAD, s + KAHEAD);
     } else {
-      put_row(s, cur);
+      put_row(s, IO::value(cur, in_dtype));  // converted here, where it is used
     }
 
     // ---- stage 5: E(s-6, c) and S(s-7, c) from the previous step's stage 4 --
@@ -519,8 +520,8 @@ struct FwdTile {
 #pragma unroll
     for (int d = 0; d < 6; ++d) C.pE[d] = 0.f;
     C.a5c = C.x6 = 0.f;
-    float pf = INB != IN_REG ? 0.f : load_row(s_begin);
-    float pf2 = INB != IN_REG ? 0.f : load_row(s_begin + 1);
+    uint32_t pf = INB != IN_REG ? 0u : load_row(s_begin);
+    uint32_t pf2 = INB != IN_REG ? 0u : load_row(s_begin + 1);
     int s = s_begin;
     oE = out_base + 2 * (int64_t)(s_begin - 7) * out_sh;  // advanced at the top of each step
     for (; s <= s_end && s - a0 < 7; s += 2) {  // pipeline fill
@@ -556,8 +557,11 @@ struct FwdTile {
 // Storage access with the types fixed at compile time.
 template <class TIn, class TOut>
 struct TypedIO {
-  __device__ __forceinline__ static float load(const void* base, int64_t idx, int) {
-    return to_float(__ldg(static_cast<const TIn*>(base) + idx));
+  __device__ __forceinline__ static uint32_t load_bits(const void* base, int64_t idx, int) {
+    return load_elem_bits(base, idx, DTypeOf<TIn>::value);
+  }
+  __device__ __forceinline__ static float value(uint32_t b, int) {
+    return elem_bits_value(b, DTypeOf<TIn>::value);
   }
   __device__ __forceinline__ static int in_size(int) { return (int)sizeof(TIn); }
   __device__ __forceinline__ static float decode(const unsigned char* p, int) {
@@ -574,8 +578,11 @@ struct TypedIO {
 
 // Storage types chosen at run time (any in/out pair).
 struct DynIO {
-  __device__ __forceinline__ static float load(const void* base, int64_t idx, int dt) {
-    return load_elem(base, idx, dt);
+  __device__ __forceinline__ static uint32_t load_bits(const void* base, int64_t idx, int dt) {
+    return load_elem_bits(base, idx, dt);
+  }
+  __device__ __forceinline__ static float value(uint32_t b, int dt) {
+    return elem_bits_value(b, dt);
   }
   __device__ __forceinline__ static int in_size(int dt) {
     return dt == DT_U8 ? 1 : (dt == DT_F32 ? 4 : 2);
