@@ -251,7 +251,7 @@ size_t weno_zoom2x_cascade_workspace_bytes(const weno_image* in, int levels,
  *     race and must be serialised by the caller.
  * Returns as weno_zoom2x_batched, plus WENO_ERANGE. */
 #define WENO_NOALLOC_MAX_IMAGES 4096
-#define WENO_NOALLOC_SCRATCH_BYTES 65600
+#define WENO_NOALLOC_SCRATCH_BYTES 32800
 int weno_zoom2x_batched_noalloc(int count, const weno_image* d_in, weno_dtype in_t,
                                 const weno_image* d_out, weno_dtype out_t, const weno_params* p,
                                 int rows_per_tile, int tile_width, void* stream);

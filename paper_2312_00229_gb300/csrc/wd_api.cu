@@ -215,8 +215,6 @@ FwdArgs make_fwd_args(const weno_image* in, int in_t, const weno_image* out, int
   const uintptr_t base = reinterpret_cast<uintptr_t>(out->data);
   a.out_vec = (out->stride_w == 1) && (out->stride_h % 2 == 0) && (out->stride_c % 2 == 0) &&
               (base % uintptr_t(2 * esz) == 0);
-  a.in_bulk = input_bulk_ok(in->data, dtype_size(in_t), in->width, in->channels,
-                            in->stride_c, in->stride_h, in->stride_w);
   return a;
 }
 
@@ -458,7 +456,6 @@ int weno_zoom2x_cascade(const weno_image* in, weno_dtype in_t, const weno_image*
     const int st = L == 0 ? int(in_t) : int(WENO_F32);
     const int dt = L + 1 == levels ? int(out_t) : int(WENO_F32);
     a.f[L] = make_fwd_args(&src, st, &dst, dt, c.n[L + 1], c.m[L + 1], c.rpb[L]);
-    a.f[L].in_bulk = 0;
     a.strips[L] = (c.m[L] + tile_width_fwd() - 1) / tile_width_fwd();
     a.bands[L] = (c.n[L] + c.rpb[L] - 1) / c.rpb[L];
     a.first[L] = first;

@@ -1,19 +1,12 @@
-// Batched forward 2x zoom: many images of independent sizes in persistent
-// launches fed by device-side tile queues.
-//
-// The images fall in two classes by input path: 1- and 2-byte storage with
-// unit column stride takes bulk row copies (class 0), anything else register
-// loads (class 1).  Each class has its own queue and persistent kernel; one
-// kernel holding both paths spills.  For 1- and 2-byte storage both kernels
-// are launched (class 1 is usually empty and exits at once); for FP32 only
-// the register kernel.
+// Batched forward 2x zoom: many images of independent sizes in one
+// persistent launch fed by a device-side tile queue.
 //
 // Workspace (caller-owned, no initialisation needed):
-//   [0]   unsigned long long  head[2], next tile of each class
-//   [16]  unsigned long long  total[2], tiles of each class
-//   [32]  unsigned long long  prefix[2][count + 1], per class the exclusive
-//                             prefix sum of the tiles of each image (0 for an
-//                             image of the other class or a malformed one)
+//   [0]   unsigned long long  head, next tile
+//   [8]   unsigned long long  total, tiles of all images
+//   [16]  unsigned long long  prefix[count + 1], the exclusive prefix sum of
+//                             the tiles of each image (a malformed image has
+//                             none)
 // The setup kernel fills it from the device-resident descriptors, so a
 // stream capture of the call replays correctly with new pixel data.
 #include "wd_batched.h"
@@ -30,19 +23,14 @@ using fwd_tile::TILE_W;
 constexpr int SETUP_THREADS = 1024;
 
 struct Queue {
-  unsigned long long head[2];
-  unsigned long long total[2];
-  unsigned long long prefix[1];  // 2 (count + 1) entries
+  unsigned long long head;
+  unsigned long long total;
+  unsigned long long prefix[1];  // count + 1 entries
 };
 
 
 __host__ __device__ __forceinline__ int64_t dsize(int dt) {
   return dt == DT_U8 ? 1 : (dt == DT_F32 ? 4 : 2);
-}
-
-// Input-path class of an image: 0 = bulk row copies, 1 = register loads.
-__device__ __forceinline__ int image_class(const weno_image& in, int in_dtype) {
-  return dsize(in_dtype) <= 2 && in.stride_w == 1 ? 0 : 1;
 }
 
 __device__ bool descriptor_ok(const weno_image& in, const weno_image& out, int out_mode) {
@@ -64,66 +52,53 @@ __device__ unsigned long long image_tiles(const weno_image& in, int64_t rpb) {
 
 __global__ void __launch_bounds__(SETUP_THREADS) batched_setup_kernel(BatchedArgs a) {
   Queue* q = static_cast<Queue*>(a.workspace);
-  __shared__ unsigned long long part[2][SETUP_THREADS];
+  __shared__ unsigned long long part[SETUP_THREADS];
   const int t = threadIdx.x;
   const int chunk = (a.count + SETUP_THREADS - 1) / SETUP_THREADS;
   const int lo = min(a.count, t * chunk), hi = min(a.count, lo + chunk);
-  unsigned long long sum0 = 0ULL, sum1 = 0ULL;
+  unsigned long long sum = 0ULL;
   for (int i = lo; i < hi; ++i) {
     const weno_image in = a.in[i], out = a.out[i];
-    if (!descriptor_ok(in, out, a.out_mode)) continue;
-    const unsigned long long n = image_tiles(in, a.rows_per_band);
-    if (image_class(in, a.in_dtype) == 0) sum0 += n; else sum1 += n;
+    if (descriptor_ok(in, out, a.out_mode)) sum += image_tiles(in, a.rows_per_band);
   }
-  part[0][t] = sum0;
-  part[1][t] = sum1;
+  part[t] = sum;
   __syncthreads();
-  // Inclusive Hillis-Steele scans of the per-thread sums of both classes.
+  // Inclusive Hillis-Steele scan of the per-thread sums.
   for (int off = 1; off < SETUP_THREADS; off <<= 1) {
-    const unsigned long long v0 = t >= off ? part[0][t - off] : 0ULL;
-    const unsigned long long v1 = t >= off ? part[1][t - off] : 0ULL;
+    const unsigned long long v = t >= off ? part[t - off] : 0ULL;
     __syncthreads();
-    part[0][t] += v0;
-    part[1][t] += v1;
+    part[t] += v;
     __syncthreads();
   }
-  unsigned long long* pre0 = q->prefix;
-  unsigned long long* pre1 = q->prefix + (a.count + 1);
-  unsigned long long run0 = part[0][t] - sum0, run1 = part[1][t] - sum1;  // exclusive starts
+  unsigned long long run = part[t] - sum;  // exclusive start
   for (int i = lo; i < hi; ++i) {
-    pre0[i] = run0;
-    pre1[i] = run1;
+    q->prefix[i] = run;
     const weno_image in = a.in[i], out = a.out[i];
-    if (!descriptor_ok(in, out, a.out_mode)) continue;
-    const unsigned long long n = image_tiles(in, a.rows_per_band);
-    if (image_class(in, a.in_dtype) == 0) run0 += n; else run1 += n;
+    if (descriptor_ok(in, out, a.out_mode)) run += image_tiles(in, a.rows_per_band);
   }
   if (t == SETUP_THREADS - 1) {
-    pre0[a.count] = part[0][t];
-    pre1[a.count] = part[1][t];
-    q->total[0] = part[0][t];
-    q->total[1] = part[1][t];
-    q->head[0] = q->head[1] = 0ULL;
+    q->prefix[a.count] = part[t];
+    q->total = part[t];
+    q->head = 0ULL;
   }
 }
 
-// CLS: the image class this kernel serves (0: bulk copies, 1: registers).
-template <int BMODE, class IO, int CLS>
+template <int BMODE, class IO>
 __global__ void __launch_bounds__(THREADS, WDWENO_FWD_MIN_BLOCKS)
     batched_fwd_kernel(BatchedArgs a, MethodConsts k) {
   __shared__ Exchange ex;
   __shared__ unsigned long long s_tile;
   __shared__ int s_img;
   Queue* q = static_cast<Queue*>(a.workspace);
-  const unsigned long long total = q->total[CLS];
-  const unsigned long long* prefix = q->prefix + CLS * (a.count + 1);
+  const unsigned long long total = q->total;
+  const unsigned long long* prefix = q->prefix;
   for (;;) {
     if (threadIdx.x == 0) {
-      const unsigned long long tile = atomicAdd(&q->head[CLS], 1ULL);
+      const unsigned long long tile = atomicAdd(&q->head, 1ULL);
       int img = -1;
       if (tile < total) {
-        // largest i with prefix[i] <= tile < prefix[i + 1] (images of the
-        // other class have no tiles here and are skipped by "largest")
+        // largest i with prefix[i] <= tile < prefix[i + 1] (images with no
+        // tiles are skipped by "largest")
         int lo = 0, hi = a.count - 1;
         while (lo < hi) {
           const int mid = (lo + hi + 1) >> 1;
@@ -162,10 +137,8 @@ __global__ void __launch_bounds__(THREADS, WDWENO_FWD_MIN_BLOCKS)
     const unsigned long long per_plane = strips * bands;
     const int64_t plane = (int64_t)(local / per_plane);
     const unsigned long long rem = local % per_plane;
-    constexpr int INB = CLS == 0 ? fwd_tile::IN_BULK_ANY : fwd_tile::IN_REG;
-    f.in_bulk = INB;
-    fwd_tile::zoom2x_fwd_tile<BMODE, IO, INB>(f, k, ex, (int64_t)(rem % strips),
-                                              (int64_t)(rem / strips), plane);
+    fwd_tile::zoom2x_fwd_tile<BMODE, IO>(f, k, ex, (int64_t)(rem % strips),
+                                         (int64_t)(rem / strips), plane);
   }
 }
 
@@ -181,25 +154,16 @@ int persistent_grid(const void* kernel) {
 }  // namespace
 
 size_t batched_workspace_bytes(int count) {
-  size_t b = 32 + 16 * (size_t(count) + 1);
+  size_t b = 16 + 8 * (size_t(count) + 1);
   return (b + 15) & ~size_t(15);
-}
-
-template <int BMODE, class IO, int CLS>
-cudaError_t launch_class(const BatchedArgs& a, const MethodConsts& k, cudaStream_t stream) {
-  const int grid = persistent_grid((const void*)batched_fwd_kernel<BMODE, IO, CLS>);
-  if (grid <= 0) return cudaErrorInvalidValue;
-  batched_fwd_kernel<BMODE, IO, CLS><<<grid, THREADS, 0, stream>>>(a, k);
-  return cudaGetLastError();
 }
 
 template <int BMODE, class IO>
 cudaError_t launch_persistent(const BatchedArgs& a, const MethodConsts& k, cudaStream_t stream) {
-  if (dsize(a.in_dtype) <= 2) {
-    const cudaError_t e = launch_class<BMODE, IO, 0>(a, k, stream);
-    if (e != cudaSuccess) return e;
-  }
-  return launch_class<BMODE, IO, 1>(a, k, stream);
+  const int grid = persistent_grid((const void*)batched_fwd_kernel<BMODE, IO>);
+  if (grid <= 0) return cudaErrorInvalidValue;
+  batched_fwd_kernel<BMODE, IO><<<grid, THREADS, 0, stream>>>(a, k);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_zoom2x_batched(const BatchedArgs& a, const MethodConsts& k, int bmode,

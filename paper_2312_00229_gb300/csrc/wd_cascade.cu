@@ -45,10 +45,6 @@ struct CascadeIO {
   __device__ __forceinline__ static float value(uint32_t b, int) {
     return elem_bits_value(b, DTypeOf<TIn>::value);
   }
-  __device__ __forceinline__ static int in_size(int) { return (int)sizeof(TIn); }
-  __device__ __forceinline__ static float decode(const unsigned char* p, int) {
-    return to_float(*reinterpret_cast<const TIn*>(p));
-  }
   __device__ __forceinline__ static void store1(void* out, int64_t idx, float v, int, int clampf) {
     store_typed<TOut>(out, idx, v, clampf);
   }
@@ -66,12 +62,6 @@ struct CascadeDynIO {
   }
   __device__ __forceinline__ static float value(uint32_t b, int dt) {
     return elem_bits_value(b, dt);
-  }
-  __device__ __forceinline__ static int in_size(int dt) {
-    return dt == DT_U8 ? 1 : (dt == DT_F32 ? 4 : 2);
-  }
-  __device__ __forceinline__ static float decode(const unsigned char* p, int dt) {
-    return fwd_tile::DynIO::decode(p, dt);
   }
   __device__ __forceinline__ static void store1(void* out, int64_t idx, float v, int dt,
                                                 int clampf) {
@@ -92,20 +82,19 @@ template <int BMODE, class TIn, class TOut>
 struct LevelTypes {
   __device__ __forceinline__ static void run(const CascadeArgs& c, int L, Exchange& ex,
                                              int64_t strip, int64_t band, int64_t plane) {
-    using fwd_tile::IN_REG;
     const FwdArgs& f = c.f[L];
     const bool first = L == 0, last = L == c.levels - 1;
     if (first && last)
-      fwd_tile::zoom2x_fwd_tile<BMODE, CascadeIO<TIn, TOut>, IN_REG>(f, c.k[L], ex, strip, band,
+      fwd_tile::zoom2x_fwd_tile<BMODE, CascadeIO<TIn, TOut>>(f, c.k[L], ex, strip, band,
                                                                      plane);
     else if (first)
-      fwd_tile::zoom2x_fwd_tile<BMODE, CascadeIO<TIn, float>, IN_REG>(f, c.k[L], ex, strip, band,
+      fwd_tile::zoom2x_fwd_tile<BMODE, CascadeIO<TIn, float>>(f, c.k[L], ex, strip, band,
                                                                       plane);
     else if (last)
-      fwd_tile::zoom2x_fwd_tile<BMODE, CascadeIO<float, TOut>, IN_REG>(f, c.k[L], ex, strip,
+      fwd_tile::zoom2x_fwd_tile<BMODE, CascadeIO<float, TOut>>(f, c.k[L], ex, strip,
                                                                        band, plane);
     else
-      fwd_tile::zoom2x_fwd_tile<BMODE, CascadeIO<float, float>, IN_REG>(f, c.k[L], ex, strip,
+      fwd_tile::zoom2x_fwd_tile<BMODE, CascadeIO<float, float>>(f, c.k[L], ex, strip,
                                                                         band, plane);
   }
 };
@@ -114,7 +103,7 @@ template <int BMODE>
 struct LevelDyn {
   __device__ __forceinline__ static void run(const CascadeArgs& c, int L, Exchange& ex,
                                              int64_t strip, int64_t band, int64_t plane) {
-    fwd_tile::zoom2x_fwd_tile<BMODE, CascadeDynIO, fwd_tile::IN_REG>(c.f[L], c.k[L], ex, strip,
+    fwd_tile::zoom2x_fwd_tile<BMODE, CascadeDynIO>(c.f[L], c.k[L], ex, strip,
                                                                     band, plane);
   }
 };

@@ -17,23 +17,18 @@ using fwd_tile::Exchange;
 using fwd_tile::THREADS;
 using fwd_tile::TILE_W;
 
-template <int BMODE, class IO, int INB>
+template <int BMODE, class IO>
 __global__ void __launch_bounds__(THREADS, WDWENO_FWD_MIN_BLOCKS)
     zoom2x_fwd_kernel(FwdArgs a, MethodConsts k) {
   __shared__ Exchange ex;
-  fwd_tile::zoom2x_fwd_tile<BMODE, IO, INB>(a, k, ex, blockIdx.x, blockIdx.y, blockIdx.z);
+  fwd_tile::zoom2x_fwd_tile<BMODE, IO>(a, k, ex, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 template <int BMODE, class IO>
 cudaError_t launch_fwd(const FwdArgs& a, const MethodConsts& k, cudaStream_t stream) {
   dim3 grid((unsigned)((a.m + TILE_W - 1) / TILE_W),
             (unsigned)((a.n + a.rows_per_band - 1) / a.rows_per_band), (unsigned)a.planes);
-  if (a.in_bulk == fwd_tile::IN_BULK_ALIGNED)
-    zoom2x_fwd_kernel<BMODE, IO, fwd_tile::IN_BULK_ALIGNED><<<grid, THREADS, 0, stream>>>(a, k);
-  else if (a.in_bulk == fwd_tile::IN_BULK_ANY)
-    zoom2x_fwd_kernel<BMODE, IO, fwd_tile::IN_BULK_ANY><<<grid, THREADS, 0, stream>>>(a, k);
-  else
-    zoom2x_fwd_kernel<BMODE, IO, fwd_tile::IN_REG><<<grid, THREADS, 0, stream>>>(a, k);
+  zoom2x_fwd_kernel<BMODE, IO><<<grid, THREADS, 0, stream>>>(a, k);
   return cudaGetLastError();
 }
 

@@ -36,16 +36,11 @@
 // One barrier (B1) opens each step: every shared value a step reads was
 // written in an earlier step, in a slot no thread writes in the same step.
 //
-// Input path (template parameter INB, see InputPath).  For 1- and 2-byte
-// storage with unit column stride, thread 0 requests each input row segment
-// of the strip (with its halo; the 16-byte blocks that cover it) KAHEAD steps
-// ahead as one asynchronous bulk copy into a ring of RING raw rows in shared
-// memory, completing on the slot's mbarrier.  At the end of step s every
-// thread waits for row s and decodes its own (clamped) column of it into the
-// float ring (first read in step s+1).  The sweep's barriers do not wait for
-// these copies, unlike register loads issued before them, so the DRAM latency
-// is covered by KAHEAD steps of work.  FP32 and strided columns (IN_REG) load
-// each row into a register two steps ahead.
+// Input: each thread loads its (clamped) column of input row s+2 in step s,
+// as the element's storage bits, and converts it to FP32 in step s+2, where
+// it publishes the row to the ring.  Nothing waits for the load until then:
+// the loaded register is only renamed in between (the step loop is unrolled
+// twice), and the barriers do not wait for loads in flight.
 #pragma once
 
 #include <cstddef>
@@ -60,14 +55,6 @@ constexpr int THREADS = 256;
 constexpr int HALO_L = 4;            // columns before the strip
 constexpr int TILE_W = THREADS - 9;  // output columns per CTA
 constexpr int ROW = THREADS + 4;     // floats per staged row (2 pad each side)
-constexpr int RING = 8;              // raw input rows in flight or in use
-constexpr int KAHEAD = 6;            // rows requested ahead of the sweep (< RING)
-// Raw bytes of one strip row: 256 columns of 1- or 2-byte storage (the only
-// sizes taken by bulk copy) widened to 16-byte blocks (at most 528 bytes).
-constexpr int RAW_BYTES = THREADS * 2 + 32;
-// Bound on one wait for an input row (nanoseconds of global time).
-constexpr unsigned long long WAIT_LIMIT_NS = 1000000000ull;
-static_assert(KAHEAD < RING && (RING & (RING - 1)) == 0, "input ring shape");
 
 struct __align__(16) Exchange {
   float A[12][ROW];           // input rows, slot = row & 7, column c at t + 2; slots
@@ -80,31 +67,18 @@ struct __align__(16) Exchange {
   float4 VS[2][THREADS + 2];  // S-point SIs summed over rows r-1, r (column c at t + 1),
                               // slot = step parity
   float4 VE[2][THREADS + 2];  // E-point SIs summed over rows r-1, r
-  // --- everything above is zeroed at the start of a tile ---
-  unsigned char raw[RING][RAW_BYTES];  // bulk-copied input rows, slot = load index % RING
-  uint64_t mbar[RING];                 // completion barrier of each slot
-  int mis[RING];                       // byte offset of the window's first column in the slot
 };
-static_assert(offsetof(Exchange, raw) % 16 == 0 && RAW_BYTES % 16 == 0, "bulk destinations");
 static_assert(sizeof(Exchange) <= 48 * 1024, "static shared memory");
 
 // Bounded waits that gave up in the kernels of this translation unit (each
-// kernel TU has its own counter; see read_wait_timeouts).
+// kernel TU has its own counter; see read_wait_timeouts).  The fused
+// cascade's waits between levels are the ones that count here.
 static __device__ unsigned int g_wait_timeouts;
 
 __device__ __forceinline__ uint64_t global_ns() {
   uint64_t t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
-}
-
-// Waits for an input row; false after WAIT_LIMIT_NS.
-__device__ __forceinline__ bool wait_row(uint64_t* bar, uint32_t parity) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const uint64_t t0 = global_ns();
-  while (!mbar_try_wait(bar, parity))
-    if (global_ns() - t0 > WAIT_LIMIT_NS) return false;
-  return true;
 }
 
 // Host side: this TU's count of abandoned waits (optionally reset to 0).
@@ -136,13 +110,7 @@ struct Carry {
   float DEp[4], DSp[4], pE[6], a5c, x6;
 };
 
-// INB: input path.  IN_REG = register loads two rows ahead; IN_BULK_ALIGNED
-// = bulk copies of rows whose starts are 16-byte aligned (one window offset
-// and length for every row); IN_BULK_ANY = bulk copies of rows that start
-// anywhere (per-row offset, published in Exchange::mis).
-enum InputPath { IN_REG = 0, IN_BULK_ALIGNED = 1, IN_BULK_ANY = 2 };
-
-template <int BMODE, class IO, int INB>
+template <int BMODE, class IO>
 struct FwdTile {
   // Arguments are held by value so that they stay in registers across the
   // barriers (a reference would be re-read from memory after each one).
@@ -159,12 +127,6 @@ struct FwdTile {
   int64_t out_sw;
   int64_t oE;                // element index of (fine row 2(s-6), fine column 2c) in step s
   bool col_ok, vec_ok, odd_ok;
-  // IN_BULK_ALIGNED: own_rel = offset of this thread's column in a raw slot,
-  //   span = bytes copied per row (the same window for every row);
-  // IN_BULK_ANY: own_rel = bytes from the window's first column to this
-  //   thread's, span = bytes of the window's columns in a row.
-  int own_rel;
-  int span;
 
   __device__ __forceinline__ FwdTile(const FwdArgs& a, const MethodConsts& k_, Exchange& ex_,
                                      int64_t bx, int64_t by, int64_t plane)
@@ -187,59 +149,6 @@ struct FwdTile {
     out_sw = a.out_sw;
     out_sh = a.out_sh;
     out_base = plane * a.out_sc + 2 * c * a.out_sw;
-    if constexpr (INB != IN_REG) {
-      // window = the strip's columns b0-4 .. b0+251 inside the image
-      const int64_t esz = IO::in_size(in_dtype);
-      const int64_t lo_c = b0 - HALO_L > 0 ? b0 - HALO_L : 0;
-      int64_t hi_c = b0 - HALO_L + THREADS;
-      if (hi_c > a.m) hi_c = a.m;
-      if constexpr (INB == IN_BULK_ALIGNED) {
-        // row starts are 16-byte aligned: the window widened to 16-byte blocks
-        const int64_t lo = (lo_c * esz) & ~int64_t(15);
-        const int64_t hi = (hi_c * esz + 15) & ~int64_t(15);
-        span = (int)(hi - lo);
-        own_rel = (int)(clamp64(c, 0, a.m - 1) * esz - lo);
-      } else {
-        span = (int)((hi_c - lo_c) * esz);
-        own_rel = (int)((clamp64(c, 0, a.m - 1) - lo_c) * esz);
-      }
-    } else {
-      span = 0;
-      own_rel = 0;
-    }
-  }
-
-  // Thread 0: requests input row r (clamped) as load number j into its slot.
-  // The copy covers the 16-byte blocks that hold the window's columns, so a
-  // row may start anywhere; a 16-byte block never straddles a page, so the
-  // bytes before and after the window that come along are mapped memory,
-  // and no thread decodes them.
-  __device__ __forceinline__ void issue_row(int j, int r) const {
-    const int rc = r < 0 ? 0 : (r > n - 1 ? n - 1 : r);
-    // thread 0's in_idx is the window's first column of row 0
-    const unsigned char* first = static_cast<const unsigned char*>(in) +
-                                 (in_idx + (int64_t)rc * in_sh) * IO::in_size(in_dtype);
-    const int slot = j & (RING - 1);
-    const unsigned char* src;
-    uint32_t len;
-    if constexpr (INB == IN_BULK_ALIGNED) {
-      src = first - own_rel;  // thread 0's offset in the slot
-      len = (uint32_t)span;
-    } else {
-      const int mis = (int)(reinterpret_cast<uintptr_t>(first) & 15);
-      src = first - mis;
-      len = (uint32_t)((mis + span + 15) & ~15);
-      ex.mis[slot] = mis;  // read KAHEAD steps later, after as many barriers
-    }
-    uint64_t* bar = &ex.mbar[slot];
-    mbar_arrive_expect_tx(bar, len);
-    bulk_g2s(ex.raw[slot], src, len, bar);
-  }
-
-  // Waits (bounded) for load number j.
-  __device__ __forceinline__ void await_row(int j) const {
-    if (!wait_row(&ex.mbar[j & (RING - 1)], (uint32_t)(j / RING) & 1u))
-      atomicAdd(&g_wait_timeouts, 1u);
   }
 
   // Storage bits of input row r (clamped), column c.
@@ -281,26 +190,12 @@ struct FwdTile {
     const float w = k.w;
     oE += 2 * out_sh;
 
-    const int j = rs + HALO_L;  // load number of row s (the sweep starts at a0 - 4)
-    uint32_t cur = 0u;
-    if constexpr (INB == IN_REG) {
-      cur = pf;               // input row s, loaded in step s-2 (storage bits)
-      pf = pf2;
-      pf2 = load_row(s + 2);  // prefetch two rows ahead
-    }
+    const uint32_t cur = pf;  // input row s, loaded in step s-2 (storage bits)
+    pf = pf2;
+    pf2 = load_row(s + 2);    // prefetch two rows ahead
 
     __syncthreads();  // B1: rows published in step s-1 are visible
-    // IN_BULK_ANY: byte offset of this thread's column in the raw slot of row
-    // s; thread 0 wrote the slot's offset when it requested the row, KAHEAD
-    // steps ago, so the barriers since then make it visible without the wait
-    int any_off = 0;
-    if constexpr (INB == IN_BULK_ANY) any_off = ex.mis[j & (RING - 1)] + own_rel;
-    if constexpr (INB != IN_REG) {
-      // the slot of load j + KAHEAD was last decoded in step s-2
-      if (t == 0 && rs >= -HALO_L && rs + KAHEAD <= H + 5) issue_row(j + KAHEAD, s + KAHEAD);
-    } else {
-      put_row(s, IO::value(cur, in_dtype));  // converted here, where it is used
-    }
+    put_row(s, IO::value(cur, in_dtype));  // converted here, where it is used
 
     // ---- stage 5: E(s-6, c) and S(s-7, c) from the previous step's stage 4 --
     // (E row r is stage-4 row s-6 of step s-1; the S blend's data pS was
@@ -473,14 +368,6 @@ struct FwdTile {
       C.a5c = a5[1];
       C.x6 = x6;
     }
-
-    if (INB != IN_REG && (FULL || (rs >= -HALO_L && rs <= H + 5))) {
-      // input row s (slot s & 7 last held row s-8, last read in step s-3);
-      // first read in step s+1, so this wait delays no barrier
-      await_row(j);
-      put_row(s, IO::decode(ex.raw[j & (RING - 1)] + (INB == IN_BULK_ANY ? any_off : own_rel),
-                            in_dtype));
-    }
   }
 
   __device__ __forceinline__ void run() {
@@ -489,7 +376,7 @@ struct FwdTile {
     __syncthreads();
     {
       float* z = reinterpret_cast<float*>(&ex);
-      for (int i = t; i < (int)(offsetof(Exchange, raw) / sizeof(float)); i += THREADS) z[i] = 0.f;
+      for (int i = t; i < (int)(sizeof(Exchange) / sizeof(float)); i += THREADS) z[i] = 0.f;
     }
     // The sweep starts on an even row, so that step<PH> runs on rows of
     // parity PH and the parity-slotted rings have compile-time indices; an
@@ -498,12 +385,6 @@ struct FwdTile {
     const int s_begin = s_first & ~1;
     const int s_last = a0 + H + 5;   // last input row of the band's sweep
     const int s_end = s_last + 1;    // inclusive: one more step finishes stage 5
-    const int loads = s_last - s_first + 1;
-    if (INB != IN_REG && t == 0) {
-      for (int i = 0; i < RING; ++i) mbar_init(&ex.mbar[i], 1);
-      fence_mbar_init();
-      for (int j = 0; j < KAHEAD && j < loads; ++j) issue_row(j, s_first + j);
-    }
     Carry C;
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
@@ -520,8 +401,8 @@ struct FwdTile {
 #pragma unroll
     for (int d = 0; d < 6; ++d) C.pE[d] = 0.f;
     C.a5c = C.x6 = 0.f;
-    uint32_t pf = INB != IN_REG ? 0u : load_row(s_begin);
-    uint32_t pf2 = INB != IN_REG ? 0u : load_row(s_begin + 1);
+    uint32_t pf = load_row(s_begin);
+    uint32_t pf2 = load_row(s_begin + 1);
     int s = s_begin;
     oE = out_base + 2 * (int64_t)(s_begin - 7) * out_sh;  // advanced at the top of each step
     for (; s <= s_end && s - a0 < 7; s += 2) {  // pipeline fill
@@ -537,20 +418,6 @@ struct FwdTile {
       step<0, false>(s, pf, pf2, C);
       step<1, false>(s + 1, pf, pf2, C);
     }
-    if (INB != IN_REG) {
-      __syncthreads();  // every thread has decoded its last row
-      if (t == 0) {
-        // Every issued row was waited for; after an abandoned wait a copy
-        // may still be in flight, so wait (bounded) for each slot's last
-        // load before the barriers are invalidated and the memory reused.
-        for (int i = 0; i < RING && i < loads; ++i) {
-          const int last = i + ((loads - 1 - i) / RING) * RING;
-          if (!wait_row(&ex.mbar[i], (uint32_t)(last / RING) & 1u)) atomicAdd(&g_wait_timeouts, 1u);
-          mbar_inval(&ex.mbar[i]);
-        }
-      }
-      __syncthreads();
-    }
   }
 };
 
@@ -562,10 +429,6 @@ struct TypedIO {
   }
   __device__ __forceinline__ static float value(uint32_t b, int) {
     return elem_bits_value(b, DTypeOf<TIn>::value);
-  }
-  __device__ __forceinline__ static int in_size(int) { return (int)sizeof(TIn); }
-  __device__ __forceinline__ static float decode(const unsigned char* p, int) {
-    return to_float(*reinterpret_cast<const TIn*>(p));
   }
   __device__ __forceinline__ static void store1(void* out, int64_t idx, float v, int, int clampf) {
     store_typed<TOut>(out, idx, v, clampf);
@@ -584,17 +447,6 @@ struct DynIO {
   __device__ __forceinline__ static float value(uint32_t b, int dt) {
     return elem_bits_value(b, dt);
   }
-  __device__ __forceinline__ static int in_size(int dt) {
-    return dt == DT_U8 ? 1 : (dt == DT_F32 ? 4 : 2);
-  }
-  __device__ __forceinline__ static float decode(const unsigned char* p, int dt) {
-    switch (dt) {
-      case DT_U8: return to_float(*p);
-      case DT_F16: return to_float(*reinterpret_cast<const __half*>(p));
-      case DT_BF16: return to_float(*reinterpret_cast<const __nv_bfloat16*>(p));
-      default: return *reinterpret_cast<const float*>(p);
-    }
-  }
   __device__ __forceinline__ static void store1(void* out, int64_t idx, float v, int dt,
                                                 int clampf) {
     store_elem(out, idx, v, dt, clampf);
@@ -605,11 +457,11 @@ struct DynIO {
   }
 };
 
-template <int BMODE, class IO, int INB>
+template <int BMODE, class IO>
 __device__ __forceinline__ void zoom2x_fwd_tile(const FwdArgs& a, const MethodConsts& k,
                                                 Exchange& ex, int64_t bx, int64_t by,
                                                 int64_t plane) {
-  FwdTile<BMODE, IO, INB> tile(a, k, ex, bx, by, plane);
+  FwdTile<BMODE, IO> tile(a, k, ex, bx, by, plane);
   tile.run();
 }
 

@@ -26,7 +26,7 @@ namespace {
 
 // Queue head, tile total and the prefix sum of tiles of up to
 // WENO_NOALLOC_MAX_IMAGES images (see batched_workspace_bytes).
-constexpr size_t kScratchBytes = 32 + 16 * (size_t(WENO_NOALLOC_MAX_IMAGES) + 1);
+constexpr size_t kScratchBytes = 16 + 8 * (size_t(WENO_NOALLOC_MAX_IMAGES) + 1);
 static_assert(kScratchBytes <= WENO_NOALLOC_SCRATCH_BYTES, "scratch too small");
 
 static __device__ __align__(256) unsigned char g_queue_scratch[WENO_NOALLOC_SCRATCH_BYTES];

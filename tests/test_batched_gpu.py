@@ -106,10 +106,10 @@ def test_batched_uneven_scenes_against_oracle():
 
 
 @pytest.mark.parametrize("dtype", [torch.uint8, torch.bfloat16])
-def test_batched_mixed_input_paths(dtype):
-    """One call whose images take both input paths: unit column stride (bulk
-    row copies, including rows at odd byte offsets) and column stride 2
-    (register loads); each equals the single-image kernel bit for bit."""
+def test_batched_mixed_layouts(dtype):
+    """One call whose images mix layouts: unit column stride (including rows
+    at odd byte offsets) and column stride 2; each equals the single-image
+    kernel bit for bit."""
     base = _images(dtype, [(37, 251), (64, 97), (5, 513), (130, 256), (1, 3)], seed=11)
     imgs = []
     for i, x in enumerate(base):

@@ -115,7 +115,7 @@ def test_bwd_rejects_bad_arguments_without_launching():
 def test_batched_rejects_bad_arguments_without_launching():
     p = B.weno_params_default()
     need = B.weno_zoom2x_batched_workspace_bytes(3)
-    assert need >= 32 + 16 * 4 and need % 16 == 0  # two class queues of count + 1 prefixes
+    assert need >= 16 + 8 * 4 and need % 16 == 0  # head, total, count + 1 prefixes
     assert B.weno_zoom2x_batched(0, None, 0, None, 0, p, None, 0, 0, 0, None) == B.WENO_OK
     assert B.weno_zoom2x_batched(-1, 1, 0, 1, 0, p, 2, need, 0, 0, None) == B.WENO_EINVAL
     assert B.weno_zoom2x_batched(3, None, 0, 1, 0, p, 2, need, 0, 0, None) == B.WENO_EINVAL

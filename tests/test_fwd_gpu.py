@@ -171,7 +171,7 @@ def test_fwd_4k_precision_sweep_sampled():
 @pytest.mark.parametrize("n,m", [(16384, 16384), (16000, 16001)])
 def test_fwd_large_planes_64bit_offsets(n, m):
     """3 x n x m uint8 input: output offsets exceed 2^31; the odd width puts
-    the rows at every 16-byte alignment (bulk copies of any row start)."""
+    the rows at every byte alignment."""
     x = torch.empty(3, n, m, dtype=torch.uint8, device=DEV)
     g = torch.Generator(device=DEV).manual_seed(7)
     x.copy_(torch.randint(0, 256, (3, n, m), device=DEV, generator=g, dtype=torch.uint8))
@@ -185,9 +185,8 @@ def test_fwd_large_planes_64bit_offsets(n, m):
     torch.cuda.empty_cache()
 
 
-# 1- and 2-byte storage with unit column stride takes the asynchronous
-# bulk-copy input path (whatever the row alignment); FP32 and strided
-# columns load rows into registers.  These widths keep rows 16-byte aligned.
+# Widths that keep every row 16-byte aligned (full vector stores of the
+# output rows at every storage type).
 ALIGNED = [(1, 16), (5, 32), (37, 496), (70, 512), (9, 1024), (130, 256)]
 
 
@@ -209,23 +208,22 @@ def test_fwd_aligned_storage_pairs(in_dt, out_dt):
     parity.compare(out, ref, out_dt)
 
 
-def _register_path_copy(xs):
-    """The same values with column stride 2: rows load through registers."""
+def _strided_copy(xs):
+    """The same values with column stride 2."""
     wide = torch.zeros(xs.shape[:-1] + (2 * xs.shape[-1],), device=DEV, dtype=xs.dtype)
     wide[..., ::2] = xs
     return wide[..., ::2]
 
 
-def test_fwd_bulk_and_register_paths_agree_bitwise():
-    """The same values through both input paths (unit column stride: rows
-    bulk-copied; column stride 2: rows loaded through registers) give
+def test_fwd_unit_and_strided_columns_agree_bitwise():
+    """The same values at unit column stride and at column stride 2 give
     bit-identical outputs for every band height, for 16-byte aligned rows
     (width 512) and for rows at every alignment (width 513, padded rows)."""
     x = torch.rand(2, 203, 513, device=DEV)
     for dt in (torch.uint8, torch.float16, torch.bfloat16):
         xs = (x * 255).to(torch.uint8) if dt == torch.uint8 else x.to(dt)
         for img in (xs[:, :, :512].contiguous(), xs, xs[:, :, :511]):
-            xv = _register_path_copy(img)
+            xv = _strided_copy(img)
             for r in (0, 1, 7, 64, 100):
                 a = api.zoom2x_fwd(img, rows_per_tile=r)
                 b = api.zoom2x_fwd(xv, rows_per_tile=r)
@@ -235,9 +233,8 @@ def test_fwd_bulk_and_register_paths_agree_bitwise():
 
 @pytest.mark.parametrize("dt", ["u8", "f16", "bf16"])
 def test_fwd_unaligned_rows_and_views(dt):
-    """Bulk copies of rows that start anywhere: odd widths, a crop that starts
-    at an odd element of an odd row, and single columns; parity with the
-    oracle."""
+    """Rows that start anywhere: odd widths, a crop that starts at an odd
+    element of an odd row, and single columns; parity with the oracle."""
     for shape in [(3, 1), (7, 13), (41, 257), (33, 499), (19, 771)]:
         A = RNG.random((2,) + shape)
         out, ref = _run(A, dt, dt)
