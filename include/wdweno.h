@@ -167,12 +167,13 @@ int weno_zoom2x_fwd_tiled(const weno_image* in, weno_dtype in_t, const weno_imag
                           weno_dtype out_t, const weno_params* p, int rows_per_tile,
                           int tile_width, void* stream);
 
-/* Number of bounded waits in the forward kernels (plain and batched) that
- * gave up on the current device since the library was loaded or the count
- * was last reset.  The forward kernels request input rows asynchronously and
- * wait for each with a time limit of one second; a wait that runs out marks
- * the outputs of that call as invalid and lets the kernel finish instead of
- * hanging.  Expected to stay 0.  Synchronises the device.
+/* Number of bounded waits in the forward kernels that gave up on the current
+ * device since the library was loaded or the count was last reset.  The
+ * waits are those of the fused cascade (weno_zoom2x_cascade), where a tile
+ * of one level waits for the tiles of the previous level it reads, with a
+ * time limit of one second; a wait that runs out marks the outputs of that
+ * call as invalid and lets the kernel finish instead of hanging.  Expected
+ * to stay 0.  Synchronises the device.
  *   count : receives the count (host pointer)
  *   reset : nonzero resets the count to 0 after reading
  * Returns WENO_OK, WENO_EINVAL (null count) or WENO_ECUDA. */

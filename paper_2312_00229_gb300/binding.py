@@ -192,7 +192,7 @@ def weno_zoom2x_cascade_workspace_bytes(inp, levels, params) -> int:
 
 
 def weno_wait_timeouts(reset: bool = False) -> int:
-    """Abandoned bounded waits of the forward kernels (raises on error)."""
+    """Abandoned bounded waits of the fused cascade's kernels (raises on error)."""
     v = ctypes.c_uint(0)
     check("weno_wait_timeouts", load().weno_wait_timeouts(ctypes.byref(v), 1 if reset else 0))
     return int(v.value)
