@@ -127,12 +127,23 @@ __global__ void __launch_bounds__(256) resample_kernel(ResampleArgs a, float eps
 // Storage access: a concrete element type, or Dyn for the run-time type.
 struct Dyn {};
 
+// Storage bits of one element and their value (the loads of a group are all
+// issued before any of them is converted).
 template <class T>
-__device__ __forceinline__ float rs_load(const void* base, int64_t idx, int dt) {
+__device__ __forceinline__ uint32_t rs_load_bits(const void* base, int64_t idx, int dt) {
   if constexpr (std::is_same<T, Dyn>::value) {
-    return load_elem(base, idx, dt);
+    return load_elem_bits(base, idx, dt);
   } else {
-    return to_float(__ldg(static_cast<const T*>(base) + idx));
+    return load_elem_bits(base, idx, DTypeOf<T>::value);
+  }
+}
+
+template <class T>
+__device__ __forceinline__ float rs_value(uint32_t b, int dt) {
+  if constexpr (std::is_same<T, Dyn>::value) {
+    return elem_bits_value(b, dt);
+  } else {
+    return elem_bits_value(b, DTypeOf<T>::value);
   }
 }
 
@@ -213,16 +224,38 @@ __global__ void __launch_bounds__(RS_THREADS) resample_tiled_kernel(ResampleArgs
   const int64_t kfirst = (int64_t)col_j[0] - 1, ifirst = (int64_t)row_i[0] - 1;
   const int wc = col_j[nc - 1] + 2 - (int)kfirst + 1;  // <= RS_WC (host checks the x scale)
   const int wr = row_i[nr - 1] + 2 - (int)ifirst + 1;  // <= a.win_rows (host sizes it)
-  // stage 0: decoded, clamped input window
+  // stage 0: decoded, clamped input window.  A thread takes 2 x 2 elements
+  // at a time (rows 8 apart, columns 32 apart) and issues their four loads
+  // before it converts any of them, so that the loads overlap.
+  constexpr int WR = RS_THREADS / 32;  // rows one pass of the warps covers
   const int64_t pbase = plane * a.in_sc;
-  for (int rr = warp; rr < wr; rr += RS_THREADS / 32) {
-    int64_t row = ifirst + rr;
-    row = row < 0 ? 0 : (row > a.n - 1 ? a.n - 1 : row);
-    const int64_t rbase = pbase + row * a.in_sh;
-    for (int k = lane; k < wc; k += 32) {
-      int64_t col = kfirst + k;
-      col = col < 0 ? 0 : (col > a.m - 1 ? a.m - 1 : col);
-      win[rr][k] = rs_load<TIn>(a.in, rbase + col * a.in_sw, a.in_dtype);
+  for (int rr0 = warp; rr0 < wr; rr0 += 2 * WR) {
+    int64_t rbase[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      int64_t row = ifirst + rr0 + u * WR;
+      row = row < 0 ? 0 : (row > a.n - 1 ? a.n - 1 : row);
+      rbase[u] = pbase + row * a.in_sh;
+    }
+    for (int k0 = lane; k0 < wc; k0 += 64) {
+      uint32_t b[2][2];
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int v = 0; v < 2; ++v) {
+          const int k = k0 + 32 * v;
+          int64_t col = kfirst + k;
+          col = col < 0 ? 0 : (col > a.m - 1 ? a.m - 1 : col);
+          b[u][v] = (rr0 + u * WR < wr && k < wc)
+                        ? rs_load_bits<TIn>(a.in, rbase[u] + col * a.in_sw, a.in_dtype)
+                        : 0u;
+        }
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int v = 0; v < 2; ++v)
+          if (rr0 + u * WR < wr && k0 + 32 * v < wc)
+            win[rr0 + u * WR][k0 + 32 * v] = rs_value<TIn>(b[u][v], a.in_dtype);
     }
   }
   __syncthreads();
