@@ -512,8 +512,8 @@ def extras(torch, np, api, scenes, dev, world, hbm_peak):
     # band height of the persistent launch chosen by the autotuner (untimed)
     from paper_2312_00229_gb300 import autotune
     tune_b = autotune.tune_batched(xs, candidates=(32, 64, 96, 128, 192, 256), reps=5)
-    rpb_b = min(tune_b, key=tune_b.get)
-    plan = api.BatchedPlan(xs, rows_per_tile=rpb_b)
+    rpb_b, tw_b = min(tune_b, key=tune_b.get)
+    plan = api.BatchedPlan(xs, rows_per_tile=rpb_b, tile_width=tw_b)
     out_px = sum((2 * t.shape[1]) * (2 * t.shape[2]) for t in xs)
     t_batched, _ = time_graph(torch, [plan.run], 20)
     plain_outs = [torch.empty_like(o) for o in plan.outputs]
@@ -525,8 +525,9 @@ def extras(torch, np, api, scenes, dev, world, hbm_peak):
                       "workload": "256 RGB images, sides uniform in [64, 1024], FP16 storage, "
                                   "one persistent launch (graph replay) vs 256 launches "
                                   "(graph replay)", "images": len(xs),
-                      "rows_per_band": rpb_b,
-                      "autotune_ms": {str(k): round(v, 4) for k, v in tune_b.items()}}
+                      "rows_per_band": rpb_b, "tile_width": tw_b,
+                      "autotune_ms": {f"{r}x{w}": round(v, 4)
+                                      for (r, w), v in tune_b.items()}}
     del xs, plan, plain_outs
     torch.cuda.empty_cache()
 

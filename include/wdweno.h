@@ -143,8 +143,10 @@ size_t weno_zoom2x_batched_workspace_bytes(int count);
  *   workspace   : device buffer of >= weno_zoom2x_batched_workspace_bytes
  *                 bytes; contents need no initialisation and are scratch
  *   rows_per_tile, tile_width : tile shape (0 = library default: 128-row
- *                 bands, 247-column strips); the autotuner chooses the band
- *                 height per size class
+ *                 bands, 247-column strips); tile_width 119 runs 128-thread
+ *                 CTAs (a smaller part of each image's last strip idles,
+ *                 which pays for narrow images); the autotuner chooses both
+ *                 per size class
  * Shapes follow weno_zoom2x_fwd per image; descriptors are read on the
  * device, so a malformed descriptor is skipped (its output is left
  * untouched) rather than reported.
@@ -158,9 +160,11 @@ int weno_zoom2x_batched(int count, const weno_image* d_in, weno_dtype in_t,
  *   rows_per_tile : coarse rows per CTA band, 1..4096 (0 = the default:
  *                   the band count that best balances the last wave of CTAs
  *                   on this GPU against the per-band pipeline fill)
- *   tile_width    : coarse output columns per CTA; 0 or 247 (the built
- *                   strip width: 256 threads, one column each, 9 of them
- *                   covering the dependency halo)
+ *   tile_width    : coarse output columns per CTA: 247 (256 threads, one
+ *                   column each, 9 of them covering the dependency halo),
+ *                   119 (128 threads), or 0 = the library's choice for the
+ *                   image width (119 when its strips leave at least 10%
+ *                   fewer threads idle)
  * Returns as weno_zoom2x_fwd, or WENO_EINVAL for an unsupported shape and
  * WENO_ERANGE when the band count exceeds 65535. */
 int weno_zoom2x_fwd_tiled(const weno_image* in, weno_dtype in_t, const weno_image* out,

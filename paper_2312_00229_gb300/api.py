@@ -111,11 +111,13 @@ def _out_like(x: torch.Tensor, params: Params, layout: str, dtype) -> torch.Tens
 
 def zoom2x_fwd(x: torch.Tensor, params: Optional[Params] = None, out_dtype=None,
                layout: str = "chw", rows_per_tile: Optional[int] = None,
-               out: Optional[torch.Tensor] = None) -> torch.Tensor:
+               out: Optional[torch.Tensor] = None, tile_width: int = 0) -> torch.Tensor:
     """Forward 2x zoom (``weno_zoom2x_fwd``); no autograd.
 
     ``rows_per_tile``: band height per CTA; None = the autotuner's cached
-    choice for this size class (see ``autotune``), 0 = the library default."""
+    choice for this size class (see ``autotune``), 0 = the library default.
+    ``tile_width``: output columns per CTA, 247 (256 threads) or 119 (128
+    threads); 0 = the library's choice for the image width."""
     params = params or Params()
     _require_cuda(x, "x")
     if x.numel() == 0:
@@ -127,7 +129,7 @@ def zoom2x_fwd(x: torch.Tensor, params: Optional[Params] = None, out_dtype=None,
         from . import autotune
         rows_per_tile = autotune.lookup(x, out.dtype, layout)
     rc = B.weno_zoom2x_fwd_tiled(image(x, layout), _DT[x.dtype], image(out, layout),
-                                 _DT[out.dtype], params.c(), rows_per_tile, 0,
+                                 _DT[out.dtype], params.c(), rows_per_tile, int(tile_width),
                                  _stream(x.device))
     B.check("weno_zoom2x_fwd", rc)
     return out
@@ -312,12 +314,13 @@ class BatchedPlan:
 
     def __init__(self, images: Sequence[torch.Tensor], params: Optional[Params] = None,
                  out_dtype=None, layout: str = "chw", rows_per_tile: int = 0,
-                 outputs: Optional[Sequence[torch.Tensor]] = None):
+                 outputs: Optional[Sequence[torch.Tensor]] = None, tile_width: int = 0):
         if len(images) == 0:
             raise ValueError("empty batch")
         self.params = params or Params()
         self.layout = layout
         self.rows_per_tile = int(rows_per_tile)
+        self.tile_width = int(tile_width)  # 0 = 247, or 119 (128-thread CTAs)
         dev = images[0].device
         in_dt = images[0].dtype
         for im in images:
@@ -345,7 +348,8 @@ class BatchedPlan:
         rc = B.weno_zoom2x_batched(self.count, ctypes.c_void_p(self.d_in.data_ptr()), self.in_t,
                                    ctypes.c_void_p(self.d_out.data_ptr()), self.out_t,
                                    self.params.c(), ctypes.c_void_p(self.workspace.data_ptr()),
-                                   self.ws_bytes, self.rows_per_tile, 0, _stream(self.device))
+                                   self.ws_bytes, self.rows_per_tile, self.tile_width,
+                                   _stream(self.device))
         B.check("weno_zoom2x_batched", rc)
         return self.outputs
 
@@ -353,10 +357,12 @@ class BatchedPlan:
 def zoom2x_batched(images: Sequence[torch.Tensor], params: Optional[Params] = None,
                    out_dtype=None, layout: str = "chw", rows_per_tile: Optional[int] = None):
     """Zooms images of independent sizes in one persistent launch."""
+    tile_width = 0
     if rows_per_tile is None:
         from . import autotune
-        rows_per_tile = autotune.lookup_batched(images, out_dtype, layout)
-    return BatchedPlan(images, params, out_dtype, layout, rows_per_tile).run()
+        rows_per_tile, tile_width = autotune.lookup_batched(images, out_dtype, layout)
+    return BatchedPlan(images, params, out_dtype, layout, rows_per_tile,
+                       tile_width=tile_width).run()
 
 
 class HostPipeline:

@@ -1,11 +1,13 @@
 """Autotuner for the tile shape of the forward and batched zoom.
 
 The CUDA kernels take the band height (coarse rows per CTA) as a run-time
-parameter; the strip width (247 columns, one thread per coarse column) is
-fixed by the build.  This module times candidate band heights on the current
-GPU with CUDA events and caches the fastest per size class in a JSON file,
-keyed by device name, storage types, layout and size class (planes and the
-image sides rounded up to powers of two).
+parameter, and the strip width (output columns per CTA, one thread per
+coarse column) as one of two built widths: 247 (256 threads) or 119 (128
+threads).  The one-launch forward picks the width from the image width; the
+batched launch takes it from the caller.  This module times candidate shapes
+on the current GPU with CUDA events and caches the fastest per size class in
+a JSON file, keyed by device name, storage types, layout and size class
+(planes and the image sides rounded up to powers of two).
 
 ``api.zoom2x_fwd(..., rows_per_tile=None)`` consults the cache; a miss uses the
 library's own default (the band count that balances the last wave of CTAs).
@@ -15,7 +17,7 @@ from __future__ import annotations
 import json
 import os
 import threading
-from typing import Dict, Iterable, Optional, Sequence
+from typing import Dict, Iterable, Optional, Sequence, Tuple
 
 import torch
 
@@ -107,28 +109,41 @@ def tune_fwd(x: torch.Tensor, params=None, out_dtype=None, layout: str = "chw",
     return times
 
 
+TILE_WIDTHS = (247, 119)
+
+
+def _batched_key(images: Sequence[torch.Tensor], out_dtype, layout: str) -> str:
+    return "|".join(["batched", _device_name(images[0].device),
+                     str(images[0].dtype), str(out_dtype or images[0].dtype), layout,
+                     str(_pow2(len(images)))])
+
+
 def tune_batched(images: Sequence[torch.Tensor], params=None, out_dtype=None,
                  layout: str = "chw", candidates: Iterable[int] = (16, 32, 64, 128),
-                 reps: int = 5) -> Dict[int, float]:
-    """Times the persistent batched launch for each band height and caches
-    the fastest under the batch's size class (dtype, layout, image count)."""
+                 widths: Iterable[int] = TILE_WIDTHS,
+                 reps: int = 5) -> Dict[Tuple[int, int], float]:
+    """Times the persistent batched launch for each (band height, tile width)
+    and caches the fastest under the batch's size class (dtype, layout, image
+    count).  Returns {(rows_per_tile, tile_width): milliseconds}."""
     from . import api
     times = {}
-    plans = {}
-    for r in candidates:
-        plans[r] = api.BatchedPlan(images, params, out_dtype, layout, rows_per_tile=r)
-        times[int(r)] = _time(plans[r].run, reps)
+    for tw in widths:
+        for r in candidates:
+            plan = api.BatchedPlan(images, params, out_dtype, layout, rows_per_tile=r,
+                                   tile_width=tw)
+            times[(int(r), int(tw))] = _time(plan.run, reps)
     best = min(times, key=times.get)
-    key = "|".join(["batched", _device_name(images[0].device),
-                    str(images[0].dtype), str(out_dtype or images[0].dtype), layout,
-                    str(_pow2(len(images)))])
-    _load()[key] = best
+    key = _batched_key(images, out_dtype, layout)
+    _load()[key] = best[0]
+    _load()[key + "|tile_width"] = best[1]
     _save()
     return times
 
 
-def lookup_batched(images: Sequence[torch.Tensor], out_dtype, layout: str) -> int:
-    key = "|".join(["batched", _device_name(images[0].device),
-                    str(images[0].dtype), str(out_dtype or images[0].dtype), layout,
-                    str(_pow2(len(images)))])
-    return _load().get(key, 0)
+def lookup_batched(images: Sequence[torch.Tensor], out_dtype,
+                   layout: str) -> Tuple[int, int]:
+    """Cached (band height, tile width) of this batch's size class, or (0, 0)
+    (the library defaults)."""
+    key = _batched_key(images, out_dtype, layout)
+    cache = _load()
+    return cache.get(key, 0), cache.get(key + "|tile_width", 0)

@@ -23,7 +23,7 @@ constexpr int64_t kDefaultRowsPerBand = 64;
 // of sides 64..1024 (77.2 Gpix/s at 64 rows, 78.7 at 128, 76.7 at 192); the
 // queue still holds some 10,000 tiles for 304 CTA slots.
 constexpr int64_t kBatchedRowsPerBand = 128;
-constexpr int kFwdCtasPerSm = 2;  // 256 threads x 128 registers
+constexpr int kFwdCtasPerSm = 2;  // 256-thread CTAs x 128 registers (twice as many at 128)
 
 int sm_count() {
   static int cached[64] = {0};
@@ -37,14 +37,23 @@ int sm_count() {
   return cached[dev];
 }
 
+// CTA width for a requested tile width (output columns per CTA): 247 -> 256
+// threads, 119 -> 128; 0 for any other width.
+int threads_for_width(int tile_width) {
+  if (tile_width == tile_width_fwd()) return threads_fwd();
+  if (tile_width == tile_width_fwd() - (threads_fwd() - 128)) return 128;
+  return 0;
+}
+
 // Band height for a one-launch forward: choose the number of bands B that
 // minimises (waves of CTAs) x (rows per band + pipeline fill), i.e. balance
 // the tail of the last wave against the fixed per-band cost.
-int64_t default_rows_per_band(int64_t n, int64_t m, int64_t planes) {
+int64_t default_rows_per_band(int64_t n, int64_t m, int64_t planes, int threads) {
   const int sms = sm_count();
   if (sms <= 0) return kDefaultRowsPerBand;
-  const int64_t slots = (int64_t)sms * kFwdCtasPerSm;
-  const int64_t strips = (m + tile_width_fwd() - 1) / tile_width_fwd();
+  const int64_t slots = (int64_t)sms * kFwdCtasPerSm * (threads_fwd() / threads);
+  const int64_t tw = threads - 9;
+  const int64_t strips = (m + tw - 1) / tw;
   const int64_t base = strips * planes;
   const int64_t fill = 7;  // extra steps per band: 4 + 5 halo rows + 2 pipeline steps
   int64_t best_rpb = n, best_cost = -1;
@@ -195,6 +204,7 @@ int check_pair(const weno_image* in, int in_t, const weno_image* out, int out_t,
 FwdArgs make_fwd_args(const weno_image* in, int in_t, const weno_image* out, int out_t,
                       int64_t orows, int64_t ocols, int64_t rows_per_band) {
   FwdArgs a;
+  a.threads = threads_fwd();
   a.in = in->data;
   a.out = out->data;
   a.in_dtype = in_t;
@@ -247,7 +257,7 @@ bool cascade_plan(const weno_image* in, int levels, const weno_params& p, Cascad
     if (c->n[L + 1] < 1 || c->m[L + 1] < 1 || c->n[L + 1] >= (int64_t(1) << 31) ||
         c->m[L + 1] >= (int64_t(1) << 31))
       return false;
-    c->rpb[L] = default_rows_per_band(c->n[L], c->m[L], in->channels);
+    c->rpb[L] = default_rows_per_band(c->n[L], c->m[L], in->channels, threads_fwd());
   }
   c->done_count = 0;
   for (int L = 0; L < levels; ++L) {
@@ -298,15 +308,17 @@ int weno_zoom2x_fwd_tiled(const weno_image* in, weno_dtype in_t, const weno_imag
   int rc = check_pair(in, in_t, out, out_t, p, &orows, &ocols);
   if (rc != WENO_OK) return rc;
   if (rows_per_tile < 0 || rows_per_tile > 4096) return WENO_EINVAL;
-  if (tile_width != 0 && tile_width != tile_width_fwd()) return WENO_EINVAL;
+  const int threads = tile_width == 0 ? fwd_threads_for(in->width) : threads_for_width(tile_width);
+  if (threads == 0) return WENO_EINVAL;
   MethodConsts k;
   int bmode;
   if (!fold_consts(p, &k, &bmode)) return WENO_EINVAL;
   const int64_t rpb = rows_per_tile > 0 ? rows_per_tile
                                         : default_rows_per_band(in->height, in->width,
-                                                                in->channels);
+                                                                in->channels, threads);
   if (bmode == B2 && direct_b2_ok(p, in_t)) bmode = B2R;
   FwdArgs a = make_fwd_args(in, in_t, out, out_t, orows, ocols, rpb);
+  a.threads = threads;
   if ((a.n + rpb - 1) / rpb > 65535) return WENO_ERANGE;
   cudaError_t e = launch_zoom2x_fwd(a, k, bmode, static_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? WENO_OK : WENO_ECUDA;
@@ -378,12 +390,14 @@ int weno_zoom2x_batched(int count, const weno_image* d_in, weno_dtype in_t,
   if (!workspace || workspace_bytes < batched_workspace_bytes(count)) return WENO_EWORKSPACE;
   if (reinterpret_cast<uintptr_t>(workspace) % 16 != 0) return WENO_EWORKSPACE;
   if (rows_per_tile < 0 || rows_per_tile > 4096) return WENO_EINVAL;
-  if (tile_width != 0 && tile_width != tile_width_fwd()) return WENO_EINVAL;
+  const int threads = tile_width == 0 ? threads_fwd() : threads_for_width(tile_width);
+  if (threads == 0) return WENO_EINVAL;
   MethodConsts k;
   int bmode;
   if (!fold_consts(p, &k, &bmode)) return WENO_EINVAL;
   if (bmode == B2 && direct_b2_ok(p, in_t)) bmode = B2R;
   BatchedArgs a;
+  a.threads = threads;
   a.count = count;
   a.in = d_in;
   a.out = d_out;

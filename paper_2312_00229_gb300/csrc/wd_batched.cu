@@ -16,9 +16,8 @@ namespace wdweno {
 
 namespace {
 
-using fwd_tile::Exchange;
 using fwd_tile::THREADS;
-using fwd_tile::TILE_W;
+using fwd_tile::THREADS_NARROW;
 
 constexpr int SETUP_THREADS = 1024;
 
@@ -44,8 +43,10 @@ __device__ bool descriptor_ok(const weno_image& in, const weno_image& out, int o
          out.channels == in.channels;
 }
 
-__device__ unsigned long long image_tiles(const weno_image& in, int64_t rpb) {
-  const unsigned long long strips = (in.width + TILE_W - 1) / TILE_W;
+// Tiles of one image for CTAs `threads` wide (threads - 9 output columns).
+__device__ unsigned long long image_tiles(const weno_image& in, int64_t rpb, int threads) {
+  const unsigned long long tw = (unsigned long long)(threads - 9);
+  const unsigned long long strips = (in.width + tw - 1) / tw;
   const unsigned long long bands = (in.height + rpb - 1) / rpb;
   return strips * bands * (unsigned long long)in.channels;
 }
@@ -59,7 +60,7 @@ __global__ void __launch_bounds__(SETUP_THREADS) batched_setup_kernel(BatchedArg
   unsigned long long sum = 0ULL;
   for (int i = lo; i < hi; ++i) {
     const weno_image in = a.in[i], out = a.out[i];
-    if (descriptor_ok(in, out, a.out_mode)) sum += image_tiles(in, a.rows_per_band);
+    if (descriptor_ok(in, out, a.out_mode)) sum += image_tiles(in, a.rows_per_band, a.threads);
   }
   part[t] = sum;
   __syncthreads();
@@ -74,7 +75,7 @@ __global__ void __launch_bounds__(SETUP_THREADS) batched_setup_kernel(BatchedArg
   for (int i = lo; i < hi; ++i) {
     q->prefix[i] = run;
     const weno_image in = a.in[i], out = a.out[i];
-    if (descriptor_ok(in, out, a.out_mode)) run += image_tiles(in, a.rows_per_band);
+    if (descriptor_ok(in, out, a.out_mode)) run += image_tiles(in, a.rows_per_band, a.threads);
   }
   if (t == SETUP_THREADS - 1) {
     q->prefix[a.count] = part[t];
@@ -83,10 +84,10 @@ __global__ void __launch_bounds__(SETUP_THREADS) batched_setup_kernel(BatchedArg
   }
 }
 
-template <int BMODE, class IO>
-__global__ void __launch_bounds__(THREADS, WDWENO_FWD_MIN_BLOCKS)
+template <int BMODE, class IO, int NT>
+__global__ void __launch_bounds__(NT, fwd_kernels::fwd_min_blocks<NT>())
     batched_fwd_kernel(BatchedArgs a, MethodConsts k) {
-  __shared__ Exchange ex;
+  __shared__ fwd_tile::ExchangeT<NT> ex;
   __shared__ unsigned long long s_tile;
   __shared__ int s_img;
   Queue* q = static_cast<Queue*>(a.workspace);
@@ -132,21 +133,22 @@ __global__ void __launch_bounds__(THREADS, WDWENO_FWD_MIN_BLOCKS)
     f.out_vec = out.stride_w == 1 && out.stride_h % 2 == 0 && out.stride_c % 2 == 0 &&
                 base % uintptr_t(2 * dsize(a.out_dtype)) == 0;
     const unsigned long long local = tile - prefix[img];
-    const unsigned long long strips = (f.m + TILE_W - 1) / TILE_W;
+    constexpr unsigned long long tw = NT - 9;
+    const unsigned long long strips = (f.m + tw - 1) / tw;
     const unsigned long long bands = (f.n + f.rows_per_band - 1) / f.rows_per_band;
     const unsigned long long per_plane = strips * bands;
     const int64_t plane = (int64_t)(local / per_plane);
     const unsigned long long rem = local % per_plane;
-    fwd_tile::zoom2x_fwd_tile<BMODE, IO>(f, k, ex, (int64_t)(rem % strips),
-                                         (int64_t)(rem / strips), plane);
+    fwd_tile::zoom2x_fwd_tile<BMODE, IO, NT>(f, k, ex, (int64_t)(rem % strips),
+                                             (int64_t)(rem / strips), plane);
   }
 }
 
-int persistent_grid(const void* kernel) {
+int persistent_grid(const void* kernel, int threads) {
   int dev = 0, sms = 0, per_sm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, THREADS, 0) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess)
     return 0;
   return sms * (per_sm > 0 ? per_sm : 1);
 }
@@ -158,12 +160,18 @@ size_t batched_workspace_bytes(int count) {
   return (b + 15) & ~size_t(15);
 }
 
+template <int BMODE, class IO, int NT>
+cudaError_t launch_width(const BatchedArgs& a, const MethodConsts& k, cudaStream_t stream) {
+  const int grid = persistent_grid((const void*)batched_fwd_kernel<BMODE, IO, NT>, NT);
+  if (grid <= 0) return cudaErrorInvalidValue;
+  batched_fwd_kernel<BMODE, IO, NT><<<grid, NT, 0, stream>>>(a, k);
+  return cudaGetLastError();
+}
+
 template <int BMODE, class IO>
 cudaError_t launch_persistent(const BatchedArgs& a, const MethodConsts& k, cudaStream_t stream) {
-  const int grid = persistent_grid((const void*)batched_fwd_kernel<BMODE, IO>);
-  if (grid <= 0) return cudaErrorInvalidValue;
-  batched_fwd_kernel<BMODE, IO><<<grid, THREADS, 0, stream>>>(a, k);
-  return cudaGetLastError();
+  if (a.threads == THREADS_NARROW) return launch_width<BMODE, IO, THREADS_NARROW>(a, k, stream);
+  return launch_width<BMODE, IO, THREADS>(a, k, stream);
 }
 
 cudaError_t launch_zoom2x_batched(const BatchedArgs& a, const MethodConsts& k, int bmode,

@@ -16,6 +16,7 @@ struct BatchedArgs {
   const weno_image* out;  // device array
   int in_dtype, out_dtype, out_mode;
   int64_t rows_per_band;
+  int threads;            // CTA width: 256 or 128
   void* workspace;        // >= batched_workspace_bytes(count), 16-byte aligned
 };
 

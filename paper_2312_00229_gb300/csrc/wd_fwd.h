@@ -18,7 +18,13 @@ struct FwdArgs {
   int64_t orows, ocols;          // output extent (2n or 2n-1, ...)
   int64_t rows_per_band;
   int out_vec;                   // unit column stride and 2-element aligned rows
+  int threads;                   // CTA width: 256 or 128 (fwd_threads_for)
 };
+
+// CTA width of a one-launch forward over images m columns wide: 128 when
+// its strips (119 output columns) leave fewer threads idle by a margin, else
+// 256 (247 output columns).
+int fwd_threads_for(int64_t m);
 
 int tile_width_fwd();
 int threads_fwd();

@@ -17,18 +17,29 @@ using fwd_tile::Exchange;
 using fwd_tile::THREADS;
 using fwd_tile::TILE_W;
 
-template <int BMODE, class IO>
-__global__ void __launch_bounds__(THREADS, WDWENO_FWD_MIN_BLOCKS)
+// CTAs resident per SM that the register budget is sized for.
+template <int NT>
+constexpr int fwd_min_blocks() {
+  return NT == THREADS ? WDWENO_FWD_MIN_BLOCKS : WDWENO_FWD_MIN_BLOCKS * THREADS / NT;
+}
+
+template <int BMODE, class IO, int NT>
+__global__ void __launch_bounds__(NT, fwd_min_blocks<NT>())
     zoom2x_fwd_kernel(FwdArgs a, MethodConsts k) {
-  __shared__ Exchange ex;
-  fwd_tile::zoom2x_fwd_tile<BMODE, IO>(a, k, ex, blockIdx.x, blockIdx.y, blockIdx.z);
+  __shared__ fwd_tile::ExchangeT<NT> ex;
+  fwd_tile::zoom2x_fwd_tile<BMODE, IO, NT>(a, k, ex, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 template <int BMODE, class IO>
 cudaError_t launch_fwd(const FwdArgs& a, const MethodConsts& k, cudaStream_t stream) {
-  dim3 grid((unsigned)((a.m + TILE_W - 1) / TILE_W),
+  const int nt = a.threads == fwd_tile::THREADS_NARROW ? fwd_tile::THREADS_NARROW : THREADS;
+  const int64_t tw = nt - 9;
+  dim3 grid((unsigned)((a.m + tw - 1) / tw),
             (unsigned)((a.n + a.rows_per_band - 1) / a.rows_per_band), (unsigned)a.planes);
-  zoom2x_fwd_kernel<BMODE, IO><<<grid, THREADS, 0, stream>>>(a, k);
+  if (nt == fwd_tile::THREADS_NARROW)
+    zoom2x_fwd_kernel<BMODE, IO, fwd_tile::THREADS_NARROW><<<grid, nt, 0, stream>>>(a, k);
+  else
+    zoom2x_fwd_kernel<BMODE, IO, THREADS><<<grid, nt, 0, stream>>>(a, k);
   return cudaGetLastError();
 }
 

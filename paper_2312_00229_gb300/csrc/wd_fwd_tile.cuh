@@ -3,11 +3,12 @@
 // (wd_batched.cu).  Method: arXiv 2312.00229, Sec. 3, Algorithms 1-2.
 //
 // Work decomposition
-//   One CTA = one plane x one strip of TILE_W = 247 coarse columns x one
-//   band of `rows_per_band` coarse rows.  256 threads; thread t owns coarse
-//   column c = b0 - 4 + t, so the CTA spans 256 columns: the 247 output
-//   columns plus the method's 4-before / 5-after dependency halo (an output
-//   quad depends on input rows and columns -4..+5).  The CTA sweeps its band
+//   One CTA = one plane x one strip of NT - 9 coarse columns x one band of
+//   `rows_per_band` coarse rows.  NT threads (256, or 128 for narrow
+//   images); thread t owns coarse column c = b0 - 4 + t, so the CTA spans NT
+//   columns: the NT - 9 output columns plus the method's 4-before / 5-after
+//   dependency halo (an output quad depends on input rows and columns
+//   -4..+5).  The CTA sweeps its band
 //   top to bottom, one coarse row per step; every stage is computed once per
 //   (row, column) of its region.
 //
@@ -51,23 +52,34 @@
 namespace wdweno {
 namespace fwd_tile {
 
+// CTA widths: NT threads, one coarse column each, cover NT - 9 output
+// columns.  256 is the default; 128 serves narrow images (a smaller part of
+// the last strip idles), with four CTAs per SM instead of two.
 constexpr int THREADS = 256;
+constexpr int THREADS_NARROW = 128;
 constexpr int HALO_L = 4;            // columns before the strip
 constexpr int TILE_W = THREADS - 9;  // output columns per CTA
-constexpr int ROW = THREADS + 4;     // floats per staged row (2 pad each side)
+template <int NT>
+struct Shape {
+  static constexpr int TW = NT - 9;   // output columns per CTA
+  static constexpr int ROW = NT + 4;  // floats per staged row (2 pad each side)
+};
 
-struct __align__(16) Exchange {
+template <int NT>
+struct __align__(16) ExchangeT {
+  static constexpr int ROW = Shape<NT>::ROW;
   float A[12][ROW];           // input rows, slot = row & 7, column c at t + 2; slots
                               // 8..11 repeat 0..3 so five consecutive rows are
                               // at consecutive slots from any start
   float X[5][ROW];            // phase-1 values, slot = row & 3, column c at t + 2; slot
                               // 4 repeats 0
-  float4 SI[2][THREADS + 2];  // phase-1 SIs (directions A, B, C, D), slot = row & 1,
+  float4 SI[2][NT + 2];       // phase-1 SIs (directions A, B, C, D), slot = row & 1,
                               // column c at t + 1
-  float4 VS[2][THREADS + 2];  // S-point SIs summed over rows r-1, r (column c at t + 1),
+  float4 VS[2][NT + 2];       // S-point SIs summed over rows r-1, r (column c at t + 1),
                               // slot = step parity
-  float4 VE[2][THREADS + 2];  // E-point SIs summed over rows r-1, r
+  float4 VE[2][NT + 2];       // E-point SIs summed over rows r-1, r
 };
+using Exchange = ExchangeT<THREADS>;
 static_assert(sizeof(Exchange) <= 48 * 1024, "static shared memory");
 
 // Bounded waits that gave up in the kernels of this translation unit (each
@@ -110,12 +122,14 @@ struct Carry {
   float DEp[4], DSp[4], pE[6], a5c, x6;
 };
 
-template <int BMODE, class IO>
+template <int BMODE, class IO, int NT>
 struct FwdTile {
+  static constexpr int TILE_W = Shape<NT>::TW;
+  static constexpr int ROW = Shape<NT>::ROW;
   // Arguments are held by value so that they stay in registers across the
   // barriers (a reference would be re-read from memory after each one).
   const MethodConsts k;
-  Exchange& ex;
+  ExchangeT<NT>& ex;
   const int t;
   const void* in;
   void* out;
@@ -128,7 +142,7 @@ struct FwdTile {
   int64_t oE;                // element index of (fine row 2(s-6), fine column 2c) in step s
   bool col_ok, vec_ok, odd_ok;
 
-  __device__ __forceinline__ FwdTile(const FwdArgs& a, const MethodConsts& k_, Exchange& ex_,
+  __device__ __forceinline__ FwdTile(const FwdArgs& a, const MethodConsts& k_, ExchangeT<NT>& ex_,
                                      int64_t bx, int64_t by, int64_t plane)
       : k(k_), ex(ex_), t(threadIdx.x) {
     in = a.in;
@@ -376,7 +390,7 @@ struct FwdTile {
     __syncthreads();
     {
       float* z = reinterpret_cast<float*>(&ex);
-      for (int i = t; i < (int)(sizeof(Exchange) / sizeof(float)); i += THREADS) z[i] = 0.f;
+      for (int i = t; i < (int)(sizeof(ExchangeT<NT>) / sizeof(float)); i += NT) z[i] = 0.f;
     }
     // The sweep starts on an even row, so that step<PH> runs on rows of
     // parity PH and the parity-slotted rings have compile-time indices; an
@@ -457,11 +471,11 @@ struct DynIO {
   }
 };
 
-template <int BMODE, class IO>
+template <int BMODE, class IO, int NT = THREADS>
 __device__ __forceinline__ void zoom2x_fwd_tile(const FwdArgs& a, const MethodConsts& k,
-                                                Exchange& ex, int64_t bx, int64_t by,
+                                                ExchangeT<NT>& ex, int64_t bx, int64_t by,
                                                 int64_t plane) {
-  FwdTile<BMODE, IO> tile(a, k, ex, bx, by, plane);
+  FwdTile<BMODE, IO, NT> tile(a, k, ex, bx, by, plane);
   tile.run();
 }
 

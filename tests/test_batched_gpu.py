@@ -1,6 +1,8 @@
 """Batched persistent launch: each image equals the single-image kernel bit
 for bit, CUDA-graph replay equals direct launches, malformed descriptors are
 skipped, and sampled windows match the oracle."""
+import ctypes
+
 import numpy as np
 import pytest
 import torch
@@ -140,3 +142,24 @@ def test_batched_fp32_with_data_bound():
     for o, s, q in zip(outs, singles, plain):
         assert torch.equal(o, s)
         assert (o - q).abs().max().item() <= 4e-6
+
+
+@pytest.mark.parametrize("dtype", [torch.uint8, torch.float16, torch.float32])
+def test_batched_narrow_ctas(dtype):
+    """The persistent launch with 128-thread CTAs (tile width 119) equals the
+    single-image kernel bit for bit for every image, edge sizes included."""
+    imgs = _images(dtype, SIZES, seed=17)
+    for rows in (0, 32):
+        outs = api.BatchedPlan(imgs, rows_per_tile=rows, tile_width=119).run()
+        singles = [api.zoom2x_fwd(x) for x in imgs]
+        torch.cuda.synchronize()
+        for x, o, s in zip(imgs, outs, singles):
+            assert torch.equal(o, s), (tuple(x.shape), rows)
+    from paper_2312_00229_gb300 import binding as B
+    plan = api.BatchedPlan(imgs[:2])
+    for tw in (1, 118, 120, 256):
+        rc = B.weno_zoom2x_batched(2, ctypes.c_void_p(plan.d_in.data_ptr()), plan.in_t,
+                                   ctypes.c_void_p(plan.d_out.data_ptr()), plan.out_t,
+                                   plan.params.c(), ctypes.c_void_p(plan.workspace.data_ptr()),
+                                   plan.ws_bytes, 0, tw, api._stream(plan.device))
+        assert rc == B.WENO_EINVAL, tw

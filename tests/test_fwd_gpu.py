@@ -314,3 +314,32 @@ def test_fwd_data_bound_selects_direct_weights():
     torch.cuda.synchronize()
     ref = parity.oracle_planes(big.double().numpy(), api.Params())
     parity.compare(out, ref, "f32", value_range=float(ref.max() - ref.min()))
+
+
+@pytest.mark.parametrize("dt", ["u8", "f16", "f32"])
+@pytest.mark.parametrize("mode", [0, 1])
+def test_fwd_narrow_and_wide_ctas_agree_bitwise(dt, mode):
+    """128-thread CTAs (119-column strips) and 256-thread CTAs (247-column
+    strips) give the same outputs bit for bit at widths that end their last
+    strip anywhere, and the narrow form matches the oracle."""
+    p = api.Params(out_mode=mode)
+    for shape in [(9, 1), (13, 118), (21, 119), (17, 120), (40, 247), (37, 512), (6, 1001)]:
+        A = RNG.random((2,) + shape)
+        x = parity.encode(A, dt).to(DEV)
+        a = api.zoom2x_fwd(x, p, tile_width=119)
+        b = api.zoom2x_fwd(x, p, tile_width=247)
+        c = api.zoom2x_fwd(x, p)  # the library's choice
+        torch.cuda.synchronize()
+        assert torch.equal(a, b) and torch.equal(a, c), (dt, mode, shape)
+    ref = parity.oracle_planes(parity.decode(x.cpu()), p)
+    parity.compare(a.cpu(), ref, dt)
+
+
+def test_fwd_rejects_other_tile_widths():
+    from paper_2312_00229_gb300 import binding as B
+    x = torch.zeros(3, 8, 8, dtype=torch.uint8, device=DEV)
+    o = torch.zeros(3, 16, 16, dtype=torch.uint8, device=DEV)
+    for tw in (1, 118, 120, 246, 248, 256, -1):
+        rc = B.weno_zoom2x_fwd_tiled(api.image(x), 0, api.image(o), 0, api.Params().c(), 0, tw,
+                                     api._stream(x.device))
+        assert rc == B.WENO_EINVAL, tw
