@@ -163,8 +163,8 @@ int weno_zoom2x_batched(int count, const weno_image* d_in, weno_dtype in_t,
  *   tile_width    : coarse output columns per CTA: 247 (256 threads, one
  *                   column each, 9 of them covering the dependency halo),
  *                   119 (128 threads), or 0 = the library's choice for the
- *                   image width (119 when its strips leave at least 10%
- *                   fewer threads idle)
+ *                   image width (119 when its strips need no more threads
+ *                   across the width than 247-column strips)
  * Returns as weno_zoom2x_fwd, or WENO_EINVAL for an unsupported shape and
  * WENO_ERANGE when the band count exceeds 65535. */
 int weno_zoom2x_fwd_tiled(const weno_image* in, weno_dtype in_t, const weno_image* out,

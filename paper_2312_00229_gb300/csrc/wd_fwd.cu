@@ -17,7 +17,7 @@ int fwd_threads_for(int64_t m) {
   const int64_t tw = fwd_tile::TILE_W, tn = fwd_tile::THREADS_NARROW - 9;
   const int64_t wide = (m + tw - 1) / tw * fwd_tile::THREADS;
   const int64_t narrow = (m + tn - 1) / tn * fwd_tile::THREADS_NARROW;
-  return 10 * narrow < 9 * wide ? fwd_tile::THREADS_NARROW : fwd_tile::THREADS;
+  return narrow <= wide ? fwd_tile::THREADS_NARROW : fwd_tile::THREADS;
 }
 
 cudaError_t launch_zoom2x_fwd(const FwdArgs& a, const MethodConsts& k, int bmode,

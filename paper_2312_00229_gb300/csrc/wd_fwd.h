@@ -22,8 +22,9 @@ struct FwdArgs {
 };
 
 // CTA width of a one-launch forward over images m columns wide: 128 when
-// its strips (119 output columns) leave fewer threads idle by a margin, else
-// 256 (247 output columns).
+// its strips (119 output columns) need no more threads across the width than
+// 256-thread strips (247 output columns), else 256 (measured: the narrow
+// form's finer grid wins when the thread counts tie).
 int fwd_threads_for(int64_t m);
 
 int tile_width_fwd();
