@@ -76,6 +76,8 @@ def parse_args():
                          "512x512x3 uint8 pixel art zoomed 8x by three 2x levels")
     ap.add_argument("--fused", action="store_true",
                     help="--case cascade8x: all levels in one persistent launch")
+    ap.add_argument("--tile-width", type=int, default=0, choices=[0, 119, 247],
+                    help="--case batched: output columns per CTA (0 = the library default)")
     ap.add_argument("--batch", type=int, default=None,
                     help="images per step of --case fwdbwd (default 32, the workload) or "
                          "--case batched (default 256, the workload)")
@@ -643,9 +645,10 @@ def run_case(args):
         count = args.batch or 256
         xs = [torch.from_numpy(scenes.planar(im)).to(dev).float().div(255).half()
               for im in scenes.uneven_batch(count)]
-        plan = api.BatchedPlan(xs)
+        plan = api.BatchedPlan(xs, tile_width=args.tile_width)
         step = plan.run
-        work = f"{count} uneven RGB FP16 images (sides 64..1024), one persistent launch"
+        work = (f"{count} uneven RGB FP16 images (sides 64..1024), one persistent launch, "
+                f"tile width {args.tile_width or 247}")
     else:
         args.batch = args.batch or 32
         xb = np.stack([scenes.planar(scenes.piecewise_smooth(512, 512, scenes.seed_for(5, i),
