@@ -351,10 +351,12 @@ def run_ours(args):
     xs = [x_host.to(dev) for _ in range(R)]
     outs = [torch.empty(C, 2 * H, 2 * W, dtype=torch.uint8, device=dev) for _ in range(R)]
     params = api.Params()
-    # The autotuner picks the band height for this size class (cached).
+    # The autotuner picks the band height and tile width for this size class
+    # (cached; zoom2x_fwd looks them up).
     from paper_2312_00229_gb300 import autotune
     tune_ms = autotune.tune_fwd(xs[0], params, out_dtype=torch.uint8)
     rpb = autotune.lookup(xs[0], torch.uint8, "chw")
+    tw = autotune.lookup_width(xs[0], torch.uint8, "chw")
     fns = [lambda i=i: api.zoom2x_fwd(xs[i], params, out=outs[i]) for i in range(R)]
 
     # warm-up (eager), then the graph of R launches
@@ -405,8 +407,8 @@ def run_ours(args):
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "storage": "u8", "out_mode": "2n x 2m",
                        "beta": 2.0, "rows_per_band": rpb or "library default",
-                       "strip_width": 247,
-                       "autotune_ms": {str(k): round(v, 4) for k, v in tune_ms.items()},
+                       "strip_width": tw or "library default (247 at this width)",
+                       "autotune_ms": {f"{r}x{w}": round(v, 4) for (r, w), v in tune_ms.items()},
                        "l2": "16 rotating input/output buffer sets (~500 MB) > 129 MB L2",
                        "launch": "CUDA graph of 16 launches, replayed",
                        "parallelism": f"replicas x{world} (no collective)"},

@@ -128,6 +128,8 @@ def zoom2x_fwd(x: torch.Tensor, params: Optional[Params] = None, out_dtype=None,
     if rows_per_tile is None:
         from . import autotune
         rows_per_tile = autotune.lookup(x, out.dtype, layout)
+        if tile_width == 0:
+            tile_width = autotune.lookup_width(x, out.dtype, layout)
     rc = B.weno_zoom2x_fwd_tiled(image(x, layout), _DT[x.dtype], image(out, layout),
                                  _DT[out.dtype], params.c(), rows_per_tile, int(tile_width),
                                  _stream(x.device))

@@ -25,6 +25,7 @@ CACHE_PATH = os.environ.get(
     "WDWENO_AUTOTUNE_CACHE",
     os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json"))
 CANDIDATES = (0, 16, 24, 32, 48, 64, 96, 128, 192)
+TILE_WIDTHS = (247, 119)  # output columns per CTA: 256 and 128 threads
 
 _lock = threading.Lock()
 _cache: Optional[Dict[str, int]] = None
@@ -79,6 +80,11 @@ def lookup(x: torch.Tensor, out_dtype, layout: str) -> int:
     return _load().get(size_class(x, out_dtype, layout), 0)
 
 
+def lookup_width(x: torch.Tensor, out_dtype, layout: str) -> int:
+    """Cached tile width for this size class, or 0 (the library's choice)."""
+    return _load().get(size_class(x, out_dtype, layout) + "|tile_width", 0)
+
+
 def _time(fn, reps: int) -> float:
     fn()
     torch.cuda.synchronize()
@@ -92,24 +98,29 @@ def _time(fn, reps: int) -> float:
 
 
 def tune_fwd(x: torch.Tensor, params=None, out_dtype=None, layout: str = "chw",
-             candidates: Iterable[int] = CANDIDATES, reps: int = 10) -> Dict[int, float]:
-    """Times each candidate band height on `x` and caches the fastest.
-    Returns {rows_per_tile: milliseconds}."""
+             candidates: Iterable[int] = CANDIDATES, widths: Iterable[int] = (0,) + TILE_WIDTHS,
+             reps: int = 10) -> Dict[Tuple[int, int], float]:
+    """Times each candidate (band height, tile width) on `x` and caches the
+    fastest (width 0 = the library's choice for the image width).
+    Returns {(rows_per_tile, tile_width): milliseconds}."""
     from . import api
     params = params or api.Params()
     odt = out_dtype or x.dtype
     out = api._out_like(x, params, layout, odt)
     times = {}
-    for r in candidates:
-        times[int(r)] = _time(lambda: api.zoom2x_fwd(x, params, layout=layout, rows_per_tile=r,
-                                                     out=out), reps)
+    for tw in widths:
+        for r in candidates:
+            times[(int(r), int(tw))] = _time(
+                lambda: api.zoom2x_fwd(x, params, layout=layout, rows_per_tile=r, out=out,
+                                       tile_width=tw), reps)
     best = min(times, key=times.get)
-    _load()[size_class(x, odt, layout)] = best
+    key = size_class(x, odt, layout)
+    _load()[key] = best[0]
+    _load()[key + "|tile_width"] = best[1]
     _save()
     return times
 
 
-TILE_WIDTHS = (247, 119)
 
 
 def _batched_key(images: Sequence[torch.Tensor], out_dtype, layout: str) -> str:
