@@ -208,11 +208,6 @@ __device__ __forceinline__ void store2_vec(void* base, int64_t idx, float v0, fl
 }
 
 // Typed variants (storage type fixed at compile time).
-__device__ __forceinline__ float to_float(uint8_t v) { return (float)v * (1.0f / 255.0f); }
-__device__ __forceinline__ float to_float(__half v) { return __half2float(v); }
-__device__ __forceinline__ float to_float(__nv_bfloat16 v) { return __bfloat162float(v); }
-__device__ __forceinline__ float to_float(float v) { return v; }
-
 template <class T> struct DTypeOf;
 template <> struct DTypeOf<uint8_t> { static constexpr int value = DT_U8; };
 template <> struct DTypeOf<__half> { static constexpr int value = DT_F16; };

@@ -44,8 +44,6 @@
 // twice), and the barriers do not wait for loads in flight.
 #pragma once
 
-#include <cstddef>
-
 #include "wd_common.cuh"
 #include "wd_fwd.h"
 
