@@ -36,11 +36,12 @@ namespace {
 
 constexpr int G = BWD_GHOST;
 // A 32 x 8 block covers 32 columns and R x 8 rows of cells: a thread takes R
-// cells of its column, 8 rows apart.  Three light kernels take four cells, so
-// a block's start-up is spread over more work; the others take one, which
-// keeps their register count (and occupancy) down (chosen by measurement).
+// cells of its column, 8 rows apart.  Three light kernels take four cells and
+// the x-stencil coefficients two, so a block's start-up is spread over more
+// work; the others take one, which keeps their register count (and
+// occupancy) down (chosen by measurement).
 constexpr int BWD_BY = 8;
-constexpr int R_XSI = 4, R_XVAL = 4, R_PSI = 1, R_PADJ = 1, R_COEF2 = 1, R_G2 = 1, R_COEF1 = 1,
+constexpr int R_XSI = 4, R_XVAL = 4, R_PSI = 1, R_PADJ = 1, R_COEF2 = 1, R_G2 = 1, R_COEF1 = 2,
               R_G1 = 1, R_FOLD = 4;
 
 // Workspace layout per plane (NE x ME cells, the cell count padded to a
