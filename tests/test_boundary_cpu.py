@@ -90,9 +90,12 @@ def test_fwd_rejects_bad_arguments_without_launching():
     m1 = B.weno_params_default()
     m1.out_mode = 1
     assert B.weno_zoom2x_fwd(good_in, 0, good_out, 0, m1, None) == B.WENO_EINVAL
-    # unsupported tile shapes
+    # unsupported tile shapes: band heights outside 0..4096, widths other than
+    # 0 (the library's choice), 247 (256-thread CTAs) and 119 (128 threads)
     assert B.weno_zoom2x_fwd_tiled(good_in, 0, good_out, 0, p, -1, 0, None) == B.WENO_EINVAL
-    assert B.weno_zoom2x_fwd_tiled(good_in, 0, good_out, 0, p, 0, 100, None) == B.WENO_EINVAL
+    assert B.weno_zoom2x_fwd_tiled(good_in, 0, good_out, 0, p, 4097, 0, None) == B.WENO_EINVAL
+    for tw in (-1, 1, 100, 118, 120, 128, 246, 248, 256):
+        assert B.weno_zoom2x_fwd_tiled(good_in, 0, good_out, 0, p, 0, tw, None) == B.WENO_EINVAL
 
 
 def test_bwd_rejects_bad_arguments_without_launching():
@@ -123,7 +126,10 @@ def test_batched_rejects_bad_arguments_without_launching():
     assert B.weno_zoom2x_batched(3, 1, 0, 1, 0, p, None, need, 0, 0, None) == B.WENO_EWORKSPACE
     assert B.weno_zoom2x_batched(3, 1, 0, 1, 0, p, 0x100, need - 16, 0, 0,
                                  None) == B.WENO_EWORKSPACE
-    assert B.weno_zoom2x_batched(3, 1, 0, 1, 0, p, 0x100, need, 0, 77, None) == B.WENO_EINVAL
+    for tw in (-1, 1, 77, 118, 120, 128, 246, 248, 256):  # widths other than 0, 247, 119
+        assert B.weno_zoom2x_batched(3, 1, 0, 1, 0, p, 0x100, need, 0, tw,
+                                     None) == B.WENO_EINVAL
+    assert B.weno_zoom2x_batched(3, 1, 0, 1, 0, p, 0x100, need, 4097, 0, None) == B.WENO_EINVAL
 
 
 def test_descriptor_folding_on_host_tensors():
