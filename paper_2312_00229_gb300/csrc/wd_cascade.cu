@@ -73,6 +73,15 @@ struct CascadeDynIO {
   }
 };
 
+// One tile of a level, compiled as a function of its own so that its
+// registers are allocated apart from the persistent loop and the other
+// levels' bodies.
+template <int BMODE, class IO>
+__device__ __noinline__ void level_tile(const FwdArgs& f, const MethodConsts& k, Exchange& ex,
+                                        int64_t strip, int64_t band, int64_t plane) {
+  fwd_tile::zoom2x_fwd_tile<BMODE, IO>(f, k, ex, strip, band, plane);
+}
+
 // The tile body of level L with the storage types of its position in the
 // chain: TIn -> FP32 first, FP32 -> FP32 between, FP32 -> TOut last
 // (TIn -> TOut for a single level).  One body per position measured faster
@@ -85,17 +94,13 @@ struct LevelTypes {
     const FwdArgs& f = c.f[L];
     const bool first = L == 0, last = L == c.levels - 1;
     if (first && last)
-      fwd_tile::zoom2x_fwd_tile<BMODE, CascadeIO<TIn, TOut>>(f, c.k[L], ex, strip, band,
-                                                                     plane);
+      level_tile<BMODE, CascadeIO<TIn, TOut>>(f, c.k[L], ex, strip, band, plane);
     else if (first)
-      fwd_tile::zoom2x_fwd_tile<BMODE, CascadeIO<TIn, float>>(f, c.k[L], ex, strip, band,
-                                                                      plane);
+      level_tile<BMODE, CascadeIO<TIn, float>>(f, c.k[L], ex, strip, band, plane);
     else if (last)
-      fwd_tile::zoom2x_fwd_tile<BMODE, CascadeIO<float, TOut>>(f, c.k[L], ex, strip,
-                                                                       band, plane);
+      level_tile<BMODE, CascadeIO<float, TOut>>(f, c.k[L], ex, strip, band, plane);
     else
-      fwd_tile::zoom2x_fwd_tile<BMODE, CascadeIO<float, float>>(f, c.k[L], ex, strip,
-                                                                        band, plane);
+      level_tile<BMODE, CascadeIO<float, float>>(f, c.k[L], ex, strip, band, plane);
   }
 };
 
