@@ -257,7 +257,7 @@ bool cascade_plan(const weno_image* in, int levels, const weno_params& p, Cascad
     if (c->n[L + 1] < 1 || c->m[L + 1] < 1 || c->n[L + 1] >= (int64_t(1) << 31) ||
         c->m[L + 1] >= (int64_t(1) << 31))
       return false;
-    c->rpb[L] = default_rows_per_band(c->n[L], c->m[L], in->channels, threads_fwd());
+    c->rpb[L] = default_rows_per_band(c->n[L], c->m[L], in->channels, CASCADE_THREADS);
   }
   c->done_count = 0;
   for (int L = 0; L < levels; ++L) {
@@ -470,7 +470,7 @@ int weno_zoom2x_cascade(const weno_image* in, weno_dtype in_t, const weno_image*
     const int st = L == 0 ? int(in_t) : int(WENO_F32);
     const int dt = L + 1 == levels ? int(out_t) : int(WENO_F32);
     a.f[L] = make_fwd_args(&src, st, &dst, dt, c.n[L + 1], c.m[L + 1], c.rpb[L]);
-    a.strips[L] = (c.m[L] + tile_width_fwd() - 1) / tile_width_fwd();
+    a.strips[L] = (c.m[L] + CASCADE_THREADS - 9 - 1) / (CASCADE_THREADS - 9);
     a.bands[L] = (c.n[L] + c.rpb[L] - 1) / c.rpb[L];
     a.first[L] = first;
     first += a.strips[L] * a.bands[L] * in->channels;

@@ -25,8 +25,8 @@ namespace wdweno {
 
 namespace {
 
-using fwd_tile::Exchange;
-using fwd_tile::THREADS;
+constexpr int THREADS = CASCADE_THREADS;
+using Exchange = fwd_tile::ExchangeT<THREADS>;
 
 constexpr unsigned long long WAIT_NS = 1000000000ull;
 constexpr int SETUP_THREADS = 256;
@@ -79,7 +79,7 @@ struct CascadeDynIO {
 template <int BMODE, class IO>
 __device__ __noinline__ void level_tile(const FwdArgs& f, const MethodConsts& k, Exchange& ex,
                                         int64_t strip, int64_t band, int64_t plane) {
-  fwd_tile::zoom2x_fwd_tile<BMODE, IO>(f, k, ex, strip, band, plane);
+  fwd_tile::zoom2x_fwd_tile<BMODE, IO, THREADS>(f, k, ex, strip, band, plane);
 }
 
 // The tile body of level L with the storage types of its position in the
@@ -108,8 +108,8 @@ template <int BMODE>
 struct LevelDyn {
   __device__ __forceinline__ static void run(const CascadeArgs& c, int L, Exchange& ex,
                                              int64_t strip, int64_t band, int64_t plane) {
-    fwd_tile::zoom2x_fwd_tile<BMODE, CascadeDynIO>(c.f[L], c.k[L], ex, strip,
-                                                                    band, plane);
+    fwd_tile::zoom2x_fwd_tile<BMODE, CascadeDynIO, THREADS>(c.f[L], c.k[L], ex, strip, band,
+                                                            plane);
   }
 };
 
@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(SETUP_THREADS)
 }
 
 template <class LEVEL>
-__global__ void __launch_bounds__(THREADS, WDWENO_FWD_MIN_BLOCKS)
+__global__ void __launch_bounds__(THREADS, fwd_kernels::fwd_min_blocks<THREADS>())
     cascade_fwd_kernel(const __grid_constant__ CascadeArgs c) {
   __shared__ Exchange ex;
   __shared__ long long s_item;

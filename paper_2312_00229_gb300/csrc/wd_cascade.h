@@ -10,6 +10,9 @@
 namespace wdweno {
 
 constexpr int CASCADE_MAX_LEVELS = 6;
+// CTA width of the fused launch (all levels); a level's strips are
+// CASCADE_THREADS - 9 output columns wide.
+constexpr int CASCADE_THREADS = 128;
 
 // One persistent launch over every tile of every level.  Tiles are numbered
 // level by level (first[L] .. first[L + 1] - 1), within a level band-major:
