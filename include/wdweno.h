@@ -249,7 +249,9 @@ size_t weno_zoom2x_cascade_workspace_bytes(const weno_image* in, int levels,
  *     images per call, larger counts return WENO_ERANGE.
  *   - The first call on a device looks up the array's device address with
  *     cudaGetSymbolAddress (that device must be current); make that first
- *     call before any stream capture.
+ *     call before any stream capture.  The address is kept for the life of
+ *     the process: after cudaDeviceReset on that device it is stale, so do
+ *     not call this entry point again in a process that reset the device.
  *   - The call allocates nothing (no cudaMalloc, cudaFree or allocating
  *     library routine).  Every call shares the one array and resets what it
  *     uses, so calls that overlap on the GPU (e.g. on two streams at once)

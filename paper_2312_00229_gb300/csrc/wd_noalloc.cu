@@ -25,9 +25,12 @@ using namespace wdweno;
 namespace {
 
 // Queue head, tile total and the prefix sum of tiles of up to
-// WENO_NOALLOC_MAX_IMAGES images (see batched_workspace_bytes).
-constexpr size_t kScratchBytes = 16 + 8 * (size_t(WENO_NOALLOC_MAX_IMAGES) + 1);
-static_assert(kScratchBytes <= WENO_NOALLOC_SCRATCH_BYTES, "scratch too small");
+// WENO_NOALLOC_MAX_IMAGES images, rounded up to 16 bytes exactly as
+// batched_workspace_bytes rounds it: the batched call checks the workspace
+// size against that rounded figure.
+constexpr size_t kQueueBytesAtMax =
+    (16 + 8 * (size_t(WENO_NOALLOC_MAX_IMAGES) + 1) + 15) & ~size_t(15);
+static_assert(kQueueBytesAtMax <= WENO_NOALLOC_SCRATCH_BYTES, "scratch too small");
 
 static __device__ __align__(256) unsigned char g_queue_scratch[WENO_NOALLOC_SCRATCH_BYTES];
 
@@ -64,6 +67,8 @@ extern "C" int weno_zoom2x_batched_noalloc(int count, const weno_image* d_in, we
   if (rc != WENO_OK) return rc;
   // The batched path clears the queue head and rewrites the prefix sums on
   // every call, so the array needs no clearing here.
-  return weno_zoom2x_batched(count, d_in, in_t, d_out, out_t, p, scratch, kScratchBytes,
-                             rows_per_tile, tile_width, stream);
+  // The whole array is offered as the workspace; the batched call checks it
+  // against batched_workspace_bytes(count), which is at most kQueueBytesAtMax.
+  return weno_zoom2x_batched(count, d_in, in_t, d_out, out_t, p, scratch,
+                             WENO_NOALLOC_SCRATCH_BYTES, rows_per_tile, tile_width, stream);
 }

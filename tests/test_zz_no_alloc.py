@@ -48,6 +48,23 @@ def test_noalloc_matches_batched_on_two_calls():
             assert torch.equal(a, b)
 
 
+def test_noalloc_at_the_image_limit():
+    # Exactly WENO_NOALLOC_MAX_IMAGES images fill the array to its bound: the
+    # call must succeed and match the workspace-taking batched call.  1x1 and
+    # 2x3 images keep it small.
+    n = B.WENO_NOALLOC_MAX_IMAGES
+    sizes = [(1, 1) if i % 2 else (2, 3) for i in range(n)]
+    imgs = _batch(7, sizes)
+    plan = api.BatchedPlan(imgs, rows_per_tile=16)
+    for o in plan.outputs:
+        o.fill_(7)
+    _noalloc(plan)
+    got = torch.cat([o.flatten() for o in plan.outputs])
+    ref = api.BatchedPlan(imgs, rows_per_tile=16).run()
+    torch.cuda.synchronize()
+    assert torch.equal(got, torch.cat([o.flatten() for o in ref]))
+
+
 def test_noalloc_rejects_too_many_images():
     p = B.weno_params_default()
     rc = B.weno_zoom2x_batched_noalloc(B.WENO_NOALLOC_MAX_IMAGES + 1, 1, 0, 1, 0, p, 0, 0, None)
