@@ -9,12 +9,14 @@ from __future__ import annotations
 
 import importlib
 
-__all__ = ["zoom2x", "zoom2x_fwd", "zoom2x_bwd", "zoom2x_batched", "Params", "lib", "scenes"]
+__all__ = ["zoom2x", "zoom2x_fwd", "zoom2x_bwd", "zoom2x_batched", "Params", "lib", "scenes",
+           "WenoZoom2x", "BatchedPlan", "HostPipeline", "cascade_zoom", "resample", "zoom_to"]
 
 
 def __getattr__(name):
     if name in ("zoom2x", "zoom2x_fwd", "zoom2x_bwd", "zoom2x_batched", "Params", "lib",
-                "WenoZoom2x", "cascade_zoom", "tensor_resample", "zoom_to"):
+                "WenoZoom2x", "BatchedPlan", "HostPipeline", "cascade_zoom", "resample",
+                "zoom_to"):
         mod = importlib.import_module(".api", __name__)
         return getattr(mod, name)
     if name in ("scenes", "binding", "api", "autotune"):
