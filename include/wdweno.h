@@ -81,6 +81,11 @@ typedef struct {
                        it does from the type alone for uint8 and FP16).  A
                        bound that the data exceed can overflow the weights
                        (inf / NaN outputs).  Must be >= 0 and finite. */
+  float nbr_c;     /* neighbour weight of the smoothed indicator D is
+                      nbr_c * h^2 in both phases (Eqs. 2DsmoothnessFinal and
+                      tezine print h^2/4; the proof of Theorem 1, Eq.
+                      DDiffOrder, uses h^2/8, which reproduces the paper's
+                      Table 1).  Default 0.125 (h^2/8); >= 0 and finite. */
 } weno_params;
 
 /* One image: `channels` planes of height x width. */
@@ -91,7 +96,8 @@ typedef struct {
 } weno_image;
 
 /* Defaults: beta 2, k_eps 1e-8, h 1, normalized SI, 2n x 2m, no clamp,
- * data_bound 0 (unknown). */
+ * data_bound 0 (unknown), nbr_c 0.125.  Start from these and change fields:
+ * a zeroed struct is not the default. */
 weno_params weno_params_default(void);
 
 /* Human-readable text of a status code (static storage). */

@@ -40,6 +40,8 @@ class OracleParams(ctypes.Structure):
         ("out_mode", ctypes.c_int),
         ("boundary", ctypes.c_int),
         ("ghost", ctypes.c_int),
+        ("nbr_c1", ctypes.c_double),
+        ("nbr_c2", ctypes.c_double),
     ]
 
 
@@ -73,6 +75,10 @@ def lib():
             L.oracle_zoom2x_planes.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
                                                ctypes.c_int64, ctypes.c_void_p,
                                                ctypes.POINTER(OracleParams)]
+            L.oracle_zoom2x_banded.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                               ctypes.c_int64, ctypes.c_void_p,
+                                               ctypes.POINTER(OracleParams), ctypes.c_int64,
+                                               ctypes.c_int]
             L.oracle_encode_u8.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
             L.oracle_encode_u8.restype = None
             L.oracle_directional.argtypes = [ctypes.c_double] * 4 + [
@@ -94,12 +100,16 @@ def lib():
 
 
 def params(beta=2.0, k_eps=1e-8, h=1.0, si_scale=SI_NORMALIZED, out_mode=OUT_2N,
-           boundary=BC_CLAMP, ghost=None) -> OracleParams:
+           boundary=BC_CLAMP, ghost=None, nbr_c=None) -> OracleParams:
+    """`nbr_c` = (phase-1, phase-2) coefficients c of the neighbour weight
+    c h^2 in D (Eqs. 2DsmoothnessFinal, tezine); None keeps the default."""
     p = lib().oracle_params_default()
     p.beta, p.k_eps, p.h = float(beta), float(k_eps), float(h)
     p.si_scale, p.out_mode, p.boundary = int(si_scale), int(out_mode), int(boundary)
     if ghost is not None:
         p.ghost = int(ghost)
+    if nbr_c is not None:
+        p.nbr_c1, p.nbr_c2 = float(nbr_c[0]), float(nbr_c[1])
     return p
 
 
@@ -108,7 +118,7 @@ def out_shape(n: int, m: int, out_mode: int = OUT_2N):
 
 
 def zoom2x(A, beta=2.0, k_eps=1e-8, h=1.0, si_scale=SI_NORMALIZED, out_mode=OUT_2N,
-           boundary=BC_CLAMP, ghost=None) -> np.ndarray:
+           boundary=BC_CLAMP, ghost=None, nbr_c=None) -> np.ndarray:
     """WD WENO 2x zoom of ``A`` (shape [..., n, m]) in float64.
 
     Leading dimensions are independent planes (channels, images)."""
@@ -120,10 +130,28 @@ def zoom2x(A, beta=2.0, k_eps=1e-8, h=1.0, si_scale=SI_NORMALIZED, out_mode=OUT_
     planes = int(np.prod(lead)) if lead else 1
     orows, ocols = out_shape(n, m, out_mode)
     U = np.empty(lead + (orows, ocols), dtype=np.float64)
-    prm = params(beta, k_eps, h, si_scale, out_mode, boundary, ghost)
+    prm = params(beta, k_eps, h, si_scale, out_mode, boundary, ghost, nbr_c)
     rc = lib().oracle_zoom2x_planes(A.ctypes.data, planes, n, m, U.ctypes.data, ctypes.byref(prm))
     if rc != 0:
         raise RuntimeError(f"oracle_zoom2x failed with code {rc}")
+    return U
+
+
+def zoom2x_banded(A, band_rows=16, threads=0, beta=2.0, k_eps=1e-8, h=1.0,
+                  si_scale=SI_NORMALIZED, out_mode=OUT_2N, nbr_c=None) -> np.ndarray:
+    """``zoom2x`` computed in row bands on `threads` host threads (0 = all
+    OpenMP threads).  Same values; used to time the oracle on many cores."""
+    A = np.ascontiguousarray(np.asarray(A, dtype=np.float64))
+    lead = A.shape[:-2]
+    n, m = A.shape[-2:]
+    planes = int(np.prod(lead)) if lead else 1
+    orows, ocols = out_shape(n, m, out_mode)
+    U = np.empty(lead + (orows, ocols), dtype=np.float64)
+    prm = params(beta, k_eps, h, si_scale, out_mode, BC_CLAMP, None, nbr_c)
+    rc = lib().oracle_zoom2x_banded(A.ctypes.data, planes, n, m, U.ctypes.data,
+                                    ctypes.byref(prm), int(band_rows), int(threads))
+    if rc != 0:
+        raise RuntimeError(f"oracle_zoom2x_banded failed with code {rc}")
     return U
 
 

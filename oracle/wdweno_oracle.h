@@ -36,6 +36,8 @@ typedef struct {
   int out_mode; /* ORACLE_OUT_*: 2n x 2m or (2n-1) x (2m-1) */
   int boundary; /* ORACLE_BC_* */
   int ghost;    /* coarse ghost cells per side; >= 5 */
+  double nbr_c1; /* phase-1 neighbour weight of D is nbr_c1 * h^2 (Eq. 2DsmoothnessFinal) */
+  double nbr_c2; /* phase-2 neighbour weight of D is nbr_c2 * h^2 (Eq. tezine) */
 } oracle_params;
 
 oracle_params oracle_params_default(void);
@@ -49,6 +51,12 @@ int oracle_zoom2x(const double* A, int64_t n, int64_t m, double* U,
 /* `planes` independent channels stored back to back. */
 int oracle_zoom2x_planes(const double* A, int64_t planes, int64_t n, int64_t m,
                          double* U, const oracle_params* p);
+
+/* oracle_zoom2x_planes computed in bands of `band_rows` quad rows (windows
+ * with the footprint's 4/5-row margins), OpenMP over (plane, band) pairs on
+ * `threads` threads (0 = OpenMP default).  Same output. */
+int oracle_zoom2x_banded(const double* A, int64_t planes, int64_t n, int64_t m, double* U,
+                         const oracle_params* p, int64_t band_rows, int threads);
 
 /* p (Eq. p) and SI (Eq. 2Dsmoothness) of one stencil with nodes at
  * t = -1, 1, 3 fine steps; scale_over_step = (length scale) / |d|. */

@@ -129,8 +129,13 @@ def _extend_index(n, G):
 
 
 def zoom2x(A: torch.Tensor, beta=2.0, k_eps=1e-8, h=1.0, si_scale=SI_NORMALIZED,
-           out_mode=OUT_2N, ghost=6) -> torch.Tensor:
+           out_mode=OUT_2N, ghost=6, nbr_c=(0.125, 0.125)) -> torch.Tensor:
     """WD WENO 2x zoom of ``A`` (..., n, m) with clamp-to-edge extension.
+
+    ``nbr_c`` = (phase 1, phase 2) coefficients c of the neighbour weight
+    c h^2 of D.  The definitions (Eqs. 2DsmoothnessFinal, tezine) print
+    h^2/4, the proof of Theorem 1 (Eq. DDiffOrder) h^2/8; h^2/8 reproduces
+    Table 1's coarse row, so it is the default.
 
     Differentiable with respect to ``A``; intended for float64."""
     n, m = A.shape[-2:]
@@ -139,8 +144,8 @@ def zoom2x(A: torch.Tensor, beta=2.0, k_eps=1e-8, h=1.0, si_scale=SI_NORMALIZED,
     E = A[..., _extend_index(n, G), :][..., :, _extend_index(m, G)]
     ne, me = n + 2 * G, m + 2 * G
     eps_h = k_eps * h * h
-    nbr_w = h * h / 4.0
-    prm = (beta, eps_h, nbr_w)
+    prm1 = (beta, eps_h, float(nbr_c[0]) * h * h)
+    prm2 = (beta, eps_h, float(nbr_c[1]) * h * h)
 
     grid = _FineGrid()
     grid.put(_Lattice(E, 0, 0))
@@ -152,7 +157,7 @@ def zoom2x(A: torch.Tensor, beta=2.0, k_eps=1e-8, h=1.0, si_scale=SI_NORMALIZED,
     R1, C1 = ne - 3, me - 3
     # c/L: normalized c = L; literal c = sqrt(2) h = L on diagonals.
     r1 = 1.0
-    (X,) = _phase(grid, [(3, 3, R1, C1)], diag, diag_nbr, r1, prm)
+    (X,) = _phase(grid, [(3, 3, R1, C1)], diag, diag_nbr, r1, prm1)
     grid.put(X)
 
     # Phase 2: "+" points, gamma_k = k pi/2, one fine step (+-1, 0) / (0, +-1).
@@ -171,7 +176,7 @@ def zoom2x(A: torch.Tensor, beta=2.0, k_eps=1e-8, h=1.0, si_scale=SI_NORMALIZED,
         (x0 + 3, y0 + 2, xr - 3, xc - 2),   # (even, odd): rows x0+3..x1-3
         (x0 + 2, y0 + 3, xr - 2, xc - 3),   # (odd, even): cols y0+3..y1-3
     ]
-    plus_e, plus_s = _phase(grid, targets, axis, axis_nbr, r2, prm)
+    plus_e, plus_s = _phase(grid, targets, axis, axis_nbr, r2, prm2)
 
     # Assemble the 2n x 2m crop; fine output (p, q) is fine (p + 2G, q + 2G).
     P0 = 2 * G

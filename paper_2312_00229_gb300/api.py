@@ -32,6 +32,8 @@ class Params:
     clamp_float : saturate float outputs to [0, 1]
     data_bound : 0, or a bound on |input| the caller guarantees (lets the
                  library take the direct beta = 2 weights for FP32/BF16 data)
+    nbr_c : neighbour weight nbr_c h^2 of D in both phases (h^2/8: the
+            reading of Eqs. 2DsmoothnessFinal/tezine that reproduces Table 1)
     """
     beta: float = 2.0
     k_eps: float = 1e-8
@@ -40,6 +42,7 @@ class Params:
     out_mode: int = B.WENO_OUT_2N
     clamp_float: bool = False
     data_bound: float = 0.0
+    nbr_c: float = 0.125
 
     def c(self) -> B.weno_params:
         p = B.weno_params()
@@ -47,6 +50,7 @@ class Params:
         p.si_scale, p.out_mode, p.clamp_float = int(self.si_scale), int(self.out_mode), int(
             bool(self.clamp_float))
         p.data_bound = float(self.data_bound)
+        p.nbr_c = float(self.nbr_c)
         return p
 
 

@@ -46,6 +46,7 @@ class weno_params(ctypes.Structure):
         ("out_mode", ctypes.c_int),
         ("clamp_float", ctypes.c_int),
         ("data_bound", ctypes.c_float),
+        ("nbr_c", ctypes.c_float),
     ]
 
 

@@ -109,11 +109,11 @@ bool overlaps(const weno_image* a, int64_t ea, const weno_image* b, int64_t eb) 
 bool fold_consts(const weno_params& p, MethodConsts* k, int* bmode) {
   if (!(p.beta >= 0.f) || !(p.k_eps >= 0.f) || !(p.h > 0.f) || !std::isfinite(p.beta) ||
       !std::isfinite(p.k_eps) || !std::isfinite(p.h) || !(p.data_bound >= 0.f) ||
-      !std::isfinite(p.data_bound))
+      !std::isfinite(p.data_bound) || !(p.nbr_c >= 0.f) || !std::isfinite(p.nbr_c))
     return false;
   if (p.si_scale != WENO_SI_NORMALIZED && p.si_scale != WENO_SI_LITERAL_SQRT2H) return false;
   const double h = p.h;
-  const double w = h * h / 4.0;
+  const double w = double(p.nbr_c) * h * h;
   const double eps_h = double(p.k_eps) * h * h;
   const double spread = 1.0 + 4.0 * w;
   k->w = float(w);
@@ -164,7 +164,7 @@ double input_bound(const weno_params& p, int in_t) {
 bool direct_b2_ok(const weno_params& p, int in_t) {
   const double v0 = input_bound(p, in_t);
   if (!(v0 > 0.0)) return false;
-  const double h = p.h, w = h * h / 4.0, eps_h = double(p.k_eps) * h * h;
+  const double h = p.h, w = double(p.nbr_c) * h * h, eps_h = double(p.k_eps) * h * h;
   const double v = 1.25 * v0 * (1.0 + 1e-3);  // slack for the approximate reciprocals
   const double si_max = 4.0 * v * v + 25.0 / 12.0 * 16.0 * v * v + eps_h;
   const double hi = (1.0 + 4.0 * w) * si_max;
@@ -285,6 +285,7 @@ weno_params weno_params_default(void) {
   p.out_mode = WENO_OUT_2N;
   p.clamp_float = 0;
   p.data_bound = 0.f;
+  p.nbr_c = 0.125f;
   return p;
 }
 

@@ -44,7 +44,7 @@ struct MethodConsts {
   float eps1;    // eps_h / (1 + 4 w), phase 1
   float eps2;    // phase 2 (divided by sqrt(2) in the literal mode, whose
                  // overall sqrt(2) factor cancels in the weights)
-  float w;       // h^2 / 4
+  float w;       // neighbour weight of D: nbr_c h^2
   float beta;
   int clamp_float;
 };

@@ -41,6 +41,7 @@ def encode(x: np.ndarray, dt: str) -> torch.Tensor:
 def oracle_planes(A: np.ndarray, params: api.Params) -> np.ndarray:
     """Oracle on [..., H, W] planes."""
     return oracle.zoom2x(A, beta=params.beta, k_eps=params.k_eps, h=params.h,
+                         nbr_c=(params.nbr_c, params.nbr_c),
                          si_scale=params.si_scale, out_mode=params.out_mode)
 
 

@@ -34,8 +34,9 @@ def test_library_exports_every_declared_symbol():
 
 def test_params_default():
     p = B.weno_params_default()
-    assert (p.beta, p.k_eps, p.h, p.si_scale, p.out_mode, p.clamp_float, p.data_bound) == (
-        pytest.approx(2.0), pytest.approx(1e-8), pytest.approx(1.0), 0, 0, 0, 0.0)
+    assert (p.beta, p.k_eps, p.h, p.si_scale, p.out_mode, p.clamp_float, p.data_bound,
+            p.nbr_c) == (pytest.approx(2.0), pytest.approx(1e-8), pytest.approx(1.0), 0, 0, 0,
+                         0.0, 0.125)
 
 
 def test_status_strings():
@@ -85,6 +86,10 @@ def test_fwd_rejects_bad_arguments_without_launching():
     for v in (-1.0, float("inf"), float("nan")):  # data_bound must be finite and >= 0
         bad = B.weno_params_default()
         bad.data_bound = v
+        assert B.weno_zoom2x_fwd(good_in, 0, good_out, 0, bad, None) == B.WENO_EINVAL
+    for v in (-0.125, float("inf"), float("nan")):  # nbr_c must be finite and >= 0
+        bad = B.weno_params_default()
+        bad.nbr_c = v
         assert B.weno_zoom2x_fwd(good_in, 0, good_out, 0, bad, None) == B.WENO_EINVAL
     # (2n-1) mode changes the expected output shape
     m1 = B.weno_params_default()
@@ -188,3 +193,9 @@ def test_api_zoom_levels_and_cpu_refusal():
         api.resample(torch.zeros(1, 4, 4), 8, 8)
     with pytest.raises(ValueError):
         api.zoom_to(torch.zeros(1, 4, 4), 8, 8)
+
+
+def test_package_exports_resolve():
+    import paper_2312_00229_gb300 as pkg
+    for name in pkg.__all__:
+        assert getattr(pkg, name) is not None, name

@@ -22,7 +22,8 @@ GRAD_TOL = 2e-4
 def _ref_grad(A: np.ndarray, G: np.ndarray, params: api.Params) -> np.ndarray:
     At = torch.from_numpy(A.copy()).requires_grad_(True)
     U = wt.zoom2x(At, beta=params.beta, k_eps=params.k_eps, h=params.h,
-                  si_scale=params.si_scale, out_mode=params.out_mode)
+                  si_scale=params.si_scale, out_mode=params.out_mode,
+                  nbr_c=(params.nbr_c, params.nbr_c))
     (g,) = torch.autograd.grad((U * torch.from_numpy(G)).sum(), At)
     return g.numpy()
 
@@ -67,7 +68,8 @@ def test_bwd_beta(beta):
 def test_bwd_params():
     A = RNG.random((1, 11, 13))
     G = RNG.normal(size=(1, 22, 26))
-    for params in (api.Params(si_scale=1), api.Params(h=0.25), api.Params(k_eps=1e-3)):
+    for params in (api.Params(si_scale=1), api.Params(h=0.25), api.Params(k_eps=1e-3),
+                   api.Params(nbr_c=0.25), api.Params(nbr_c=0.5, h=2.0)):
         _check(A, G, params)
 
 

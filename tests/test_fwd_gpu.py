@@ -64,7 +64,9 @@ def test_fwd_beta(beta):
 def test_fwd_literal_si_scale_and_h():
     A = RNG.random((1, 29, 243))
     for prm in (api.Params(si_scale=1), api.Params(h=1 / 64), api.Params(h=0.37, si_scale=1),
-                api.Params(k_eps=1e-4), api.Params(k_eps=0.0, h=0.5)):
+                api.Params(k_eps=1e-4), api.Params(k_eps=0.0, h=0.5),
+                api.Params(nbr_c=0.25), api.Params(nbr_c=0.0, h=2.0),
+                api.Params(nbr_c=0.25, si_scale=1)):
         out, ref = _run(A, "f32", "f32", prm)
         parity.compare(out, ref, "f32")
 
