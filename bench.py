@@ -1,20 +1,22 @@
 #!/usr/bin/env python
 """Benchmark of the GB300 WD WENO 2x zoom (arXiv 2312.00229, Sec. 3).
 
-Headline (one JSON line on rank 0): forward 2x zoom of a 1920x1080 RGB
-uint8 piecewise-smooth scene to 3840x2160, FP32 arithmetic, output Gpix/s
-(output pixels of all channels counted once per pixel), inputs resident in
-HBM.  One step = one launch of the fused forward kernel over the whole image.
-16 input/output buffer sets (~500 MB) rotate so that no step finds its data
-in the 129 MB L2; the launches are replayed from a CUDA graph.
+Headline (one JSON line on rank 0): forward 2x zoom of 3840x2160 RGB uint8
+piecewise-smooth frames to 7680x4320, FP32 arithmetic, output Gpix/s (output
+pixels of all channels counted once per pixel), inputs resident in HBM.  One
+step = one batch of FRAMES_PER_STEP frames, one launch of the fused forward
+kernel per frame; `--steps K` times exactly K such steps.  8 input/output
+buffer sets (~1 GB) rotate so that no launch finds its data in the 129 MB L2;
+the launches are replayed from a CUDA graph.
 
 The same line carries the roofline of the forward kernel, the FP64 CPU
-oracle timed on the host cores (cpu_baseline), the end-to-end figure through
-the public API with host buffers (e2e), clocks sampled during the timed
-region, and the other parts of the metric: fwd+bwd Gpix/s (32x3x512x512 FP32,
-autograd step with an L2 loss), batched vs plain (256 uneven FP16 images in
-one persistent launch), the storage-format sweep on 3840x2160x3 and the 8x
-cascade of a 512x512 pixel-art image.
+oracle timed on the host cores (cpu_baseline: one thread, and all cores over
+row bands), the end-to-end figure through the public API with host buffers
+(e2e), clocks sampled during the timed region, and the other parts of the
+metric: fwd+bwd Gpix/s (32x3x512x512 FP32, autograd step with an L2 loss),
+batched vs plain (256 uneven FP16 images in one persistent launch), the
+storage-format sweep on 3840x2160x3, the 1920x1080 frame, the 8x cascade of
+a 512x512 pixel-art image and the tensor-WENO resampling.
 
 ``--impl reference`` times the FP64 oracle (the only other implementation
 of this method; the paper's own code is not published) on the host cores
@@ -39,9 +41,11 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "2x WENO zoom output Gpix/s & %HBM roofline; fwd+bwd Gpix/s; batched vs plain"
-WORKLOAD = "1920x1080x3 uint8 piecewise-smooth scene -> 3840x2160x3 uint8, FP32 arithmetic"
-H, W, C = 1080, 1920, 3
-OUT_PX = (2 * H) * (2 * W)  # output pixels per step (all channels per pixel)
+WORKLOAD = "3840x2160x3 uint8 piecewise-smooth scene -> 7680x4320x3 uint8, FP32 arithmetic"
+H, W, C = 2160, 3840, 3
+OUT_PX = (2 * H) * (2 * W)  # output pixels per frame (all channels per pixel)
+FRAMES_PER_STEP = 256       # one step = a batch of 256 frames (8.5 s of 30 fps video)
+ROTATING_SETS = 8           # input + output buffer sets in rotation (~1 GB > L2)
 # Algorithmic FP32 operations per input pixel-channel (FMA counted once) of
 # the fused forward pass, beta = 2: stage 1: 8, stage 2: 12, stage 3: 30,
 # stage 4: 40, stage 5: 52 (plus 15 MUFU reciprocals, not counted here).
@@ -50,7 +54,7 @@ ALGO_MUFU_PER_PXCH = 15
 # Algorithmic HBM bytes per input pixel-channel: 1 read + 4 written (uint8).
 ALGO_BYTES_PER_PXCH = {"u8": 5, "f16": 10, "bf16": 10, "f32": 20}
 FP32_LANES_PER_SM = 128
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "zoom2x_fwd_1080p_u8.md")
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "zoom2x_fwd_4k_u8.md")
 # The forward kernel's code: its tile body, device helpers and kernel
 # template (the .cu files around them only choose which instantiation runs).
 KERNEL_SOURCES = ["paper_2312_00229_gb300/csrc/wd_fwd_tile.cuh",
@@ -61,16 +65,17 @@ KERNEL_SOURCES = ["paper_2312_00229_gb300/csrc/wd_fwd_tile.cuh",
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10000)
-    ap.add_argument("--warmup", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--skip-extras", action="store_true",
                     help="headline only (no fwd+bwd / batched / sweep / cascade)")
-    ap.add_argument("--case", choices=["headline", "resample3x", "fwdbwd", "batched",
+    ap.add_argument("--case", choices=["headline", "fwd4k", "resample3x", "fwdbwd", "batched",
                                        "cascade8x"],
                     default="headline",
-                    help="run one secondary workload alone (for profiling) instead of the "
-                         "headline line: resample3x = 1920x1080x3 uint8 -> 5760x3240 tensor "
+                    help="run one workload alone (for profiling) instead of the headline "
+                         "line: fwd4k = the headline forward launch, eager, over the rotating "
+                         "buffer sets; resample3x = 1920x1080x3 uint8 -> 5760x3240 tensor "
                          "WENO; fwdbwd = one autograd step on Bx3x512x512 FP32; batched = "
                          "one persistent launch over B uneven FP16 RGB images; cascade8x = "
                          "512x512x3 uint8 pixel art zoomed 8x by three 2x levels")
@@ -227,20 +232,68 @@ def max_over_ranks(world, value, device):
 # ---------------------------------------------------------------------------
 # CPU oracle (FP64) timing
 # ---------------------------------------------------------------------------
-def oracle_time_frames(frames: int, A01):
+def cpu_model():
+    """CPU model name from /proc/cpuinfo (x86 'model name'; Arm machines report
+    implementer / part numbers instead)."""
+    try:
+        text = open("/proc/cpuinfo").read()
+    except OSError:
+        return "unknown"
+    m = re.search(r"^model name\s*:\s*(.+)$", text, re.M)
+    if m:
+        return m.group(1).strip()
+    imp = re.search(r"^CPU implementer\s*:\s*(\S+)", text, re.M)
+    part = re.search(r"^CPU part\s*:\s*(\S+)", text, re.M)
+    if imp and part:
+        names = {("0x41", "0xd4f"): "Arm Neoverse V2 (NVIDIA Grace)"}
+        return names.get((imp.group(1), part.group(1)),
+                         f"Arm implementer {imp.group(1)} part {part.group(1)}")
+    return "unknown"
+
+
+# quad rows per band of the all-core oracle leg: margins of 9 rows per band
+# make a 64-row band 14% more work than the whole image
+ORACLE_BAND_ROWS = 64
+
+
+def oracle_sample(A01, rows):
+    """Input rows [r0, r0 + rows) of every plane plus the footprint margins
+    (4 rows before, 5 after); the oracle's output rows 2*4 .. 2*(4 + rows)
+    of the window are the frame's output rows 2*r0 .. 2*(r0 + rows)."""
+    r0 = max(4, (A01.shape[-2] - rows) // 2)
+    return A01[..., r0 - 4:r0 + rows + 5, :], r0
+
+
+def cpu_baseline(A01, single_rows=512, all_core_rows=H):
+    """The FP64 C oracle on the host: one thread on a band of `single_rows`
+    input rows, and all `nproc` cores (OpenMP over plane x 64-row band) on a
+    band of `all_core_rows` rows; Gpix/s of output pixels of all channels.
+    The oracle's loops are its plain own; only the partition is added."""
     import oracle
-    t0 = time.perf_counter()
-    for _ in range(frames):
-        oracle.zoom2x(A01)
-    return time.perf_counter() - t0
-
-
-def cpu_baseline_full_frames(A01, frames=3):
-    dt = oracle_time_frames(frames, A01)
-    return {"value": round(frames * OUT_PX / dt / 1e9, 6), "unit": "Gpix/s",
-            "cores": min(C, os.cpu_count() or 1), "kind": "oracle",
-            "sample": f"{frames} full 1920x1080x3 frames through the FP64 C oracle "
-                      f"(OpenMP over the 3 channel planes), {dt:.1f} s"}
+    nproc = os.cpu_count() or 1
+    n, m = A01.shape[-2:]
+    out = {}
+    for key, rows, threads, band in (("single_thread", single_rows, 1, 1 << 30),
+                                     ("all_cores", all_core_rows, nproc, ORACLE_BAND_ROWS)):
+        rows = min(rows, n - 9)
+        win, _ = oracle_sample(A01, rows)
+        t0 = time.perf_counter()
+        oracle.zoom2x_banded(win, band_rows=min(band, win.shape[-2]), threads=threads)
+        dt = time.perf_counter() - t0
+        px = (2 * rows) * (2 * m)  # the window's interior output rows
+        # the window's margin rows are computed too: count only the kept rows
+        out[key] = {"value": round(px / dt / 1e9, 6), "threads": threads, "seconds": round(dt, 2),
+                    "rows": rows}
+    return {"value": out["all_cores"]["value"], "unit": "Gpix/s",
+            "cores": nproc, "threads": nproc, "nproc": nproc, "cpu_model": cpu_model(),
+            "kind": "oracle",
+            "single_thread": out["single_thread"],
+            "all_cores": out["all_cores"],
+            "sample": f"FP64 C oracle on input rows of the {W}x{H}x{C} frame: "
+                      f"{out['single_thread']['rows']} rows on one thread, "
+                      f"{out['all_cores']['rows']} rows on {nproc} threads (OpenMP over "
+                      f"plane x {ORACLE_BAND_ROWS}-row bands, each band's window with the "
+                      f"4/5-row footprint margins); value = all cores"}
 
 
 def run_reference(args):
@@ -252,48 +305,40 @@ def run_reference(args):
     import oracle
     from paper_2312_00229_gb300 import scenes
     oracle.build()
-    img = scenes.piecewise_smooth(H, W, seed=scenes.seed_for(2))
+    img = scenes.piecewise_smooth(H, W, seed=scenes.seed_for(4))
     A01 = scenes.planar(img).astype(np.float64) / 255.0
+    nproc = os.cpu_count() or 1
     # Size each step's sample so that warm-up + timed steps fit in about two
-    # minutes.  A sample is a window of `rows` x `cols` input cells plus the
-    # method's footprint margins (4 cells before, 5 after); its output is
-    # 2 rows x 2 cols pixels.  Cost model: time per extended cell of the
-    # oracle's own grid (the window plus its 6 ghost cells per side).
-    probe_rows = 16
-    probe = A01[:, 500 - 4:500 + probe_rows + 5]
+    # minutes.  A sample is a band of `rows` input rows of every plane plus
+    # the method's footprint margins (4 rows before, 5 after); its output is
+    # 2 rows x 2 W pixels of each plane.  Cost model: a probe band.
+    probe_rows = 64
+    probe, _ = oracle_sample(A01, probe_rows)
     t0 = time.perf_counter()
-    oracle.zoom2x(probe)
-    t_probe = time.perf_counter() - t0
-    t_cell = t_probe / ((probe.shape[1] + 12) * (W + 12))
+    oracle.zoom2x_banded(probe, band_rows=ORACLE_BAND_ROWS, threads=nproc)
+    t_row = (time.perf_counter() - t0) / probe_rows
     budget = 120.0 / max(1, args.steps + args.warmup)
-    rows = int(budget / (t_cell * (W + 12))) - 21
-    cols = W
-    if rows < 1:
-        rows = 1
-        cols = int(max(16, min(W - 9, budget / (t_cell * 22) - 21)))
-    rows = min(rows, H - 9)
-    r0 = max(4, min(200, H - 5 - rows))
-    c0 = 0 if cols == W else 4
-    sample = A01[:, r0 - 4:r0 + rows + 5, max(0, c0 - 4):c0 + cols + (5 if cols < W else 0)]
+    rows = int(max(1, min(H - 9, budget / t_row)))
+    sample, r0 = oracle_sample(A01, rows)
     for _ in range(args.warmup):
-        oracle.zoom2x(sample)
+        oracle.zoom2x_banded(sample, band_rows=ORACLE_BAND_ROWS, threads=nproc)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        oracle.zoom2x(sample)
+        oracle.zoom2x_banded(sample, band_rows=ORACLE_BAND_ROWS, threads=nproc)
     dt = time.perf_counter() - t0
-    out_px = args.steps * (2 * rows) * (2 * cols)
+    out_px = args.steps * (2 * rows) * (2 * W)
     value = out_px / dt / 1e9
-    desc = (f"each step: output of input rows {r0}..{r0 + rows - 1} x {cols} columns x 3 "
-            f"channels of the 1920x1080 scene (window + 4/5-cell footprint margins), FP64 C "
-            f"oracle, OpenMP over the channel planes")
+    desc = (f"each step: output of input rows {r0}..{r0 + rows - 1} (all {W} columns, 3 "
+            f"channels) of the {W}x{H} scene, FP64 C oracle on {nproc} threads (OpenMP over "
+            f"plane x {ORACLE_BAND_ROWS}-row bands with the 4/5-row footprint margins)")
     line = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "Gpix/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(dt / args.steps * 1e3, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "implementation": "FP64 CPU oracle"},
             "cpu_baseline": {"value": round(value, 6), "unit": "Gpix/s",
-                             "cores": min(C, os.cpu_count() or 1), "kind": "oracle",
-                             "sample": desc},
+                             "cores": nproc, "threads": nproc, "cpu_model": cpu_model(),
+                             "kind": "oracle", "sample": desc},
             "e2e": {"value": round(value, 6), "unit": "Gpix/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -345,9 +390,9 @@ def run_ours(args):
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     alu_peak = sms * FP32_LANES_PER_SM * sm_max_mhz * 1e6  # FP32 ops/s
 
-    img = scenes.piecewise_smooth(H, W, seed=scenes.seed_for(2))
+    img = scenes.piecewise_smooth(H, W, seed=scenes.seed_for(4))
     x_host = torch.from_numpy(scenes.planar(img))
-    R = 16
+    R = ROTATING_SETS
     xs = [x_host.to(dev) for _ in range(R)]
     outs = [torch.empty(C, 2 * H, 2 * W, dtype=torch.uint8, device=dev) for _ in range(R)]
     params = api.Params()
@@ -357,15 +402,14 @@ def run_ours(args):
     tune_ms = autotune.tune_fwd(xs[0], params, out_dtype=torch.uint8)
     rpb = autotune.lookup(xs[0], torch.uint8, "chw")
     tw = autotune.lookup_width(xs[0], torch.uint8, "chw")
-    fns = [lambda i=i: api.zoom2x_fwd(xs[i], params, out=outs[i]) for i in range(R)]
+    # one graph = one step: FRAMES_PER_STEP launches cycling through the R sets
+    fns = [lambda i=i: api.zoom2x_fwd(xs[i % R], params, out=outs[i % R])
+           for i in range(FRAMES_PER_STEP)]
 
-    # warm-up (eager), then the graph of R launches
-    for i in range(max(args.warmup, 3)):
-        fns[i % R]()
-    torch.cuda.synchronize()
-    reps = max(1, -(-args.steps // R))
-    steps = reps * R
-    _, graph = time_graph(torch, fns, 1, warm=1)
+    # warm-up: W untimed steps (the first also captures the graph)
+    _, graph = time_graph(torch, fns, 1, warm=max(args.warmup, 3))
+    steps = args.steps
+    frames = steps * FRAMES_PER_STEP
 
     sampler = ClockSampler(local)
     sampler.start()
@@ -374,7 +418,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
-    for _ in range(reps):
+    for _ in range(steps):
         graph.replay()
     e1.record()
     torch.cuda.synchronize()
@@ -382,37 +426,49 @@ def run_ours(args):
     clocks = sampler.stop()
     t_local = e0.elapsed_time(e1) / 1e3
     t = max_over_ranks(world, t_local, dev)
-    value = replica_value(world, steps, OUT_PX, t)
-    per_launch = t_local / steps
+    value = replica_value(world, frames, OUT_PX, t)
+    per_launch = t_local / frames
 
     pxch = H * W * C
     achieved_ops = ALGO_FP32_OPS_PER_PXCH * pxch / per_launch
     achieved_gbs = ALGO_BYTES_PER_PXCH["u8"] * pxch / per_launch / 1e9
     traffic = profiled_traffic()
+    sm_med = clocks.get("sm_mhz")
     roofline = {"bound": "alu", "achieved": round(achieved_ops / 1e12, 3),
                 "peak": round(alu_peak / 1e12, 3), "unit": "Top/s",
                 "frac": round(achieved_ops / alu_peak, 4), "traffic": traffic,
                 "kernel": "zoom2x_fwd_kernel<B2R, u8->u8>",
                 "ops_per_pxch": ALGO_FP32_OPS_PER_PXCH,
+                "peak_kind": "nominal FP32-pipe peak (not measured): SMs x 128 lanes x "
+                             "maximum SM clock",
                 "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_max_mhz:.0f} MHz",
+                "sm_mhz_median_timed": sm_med,
+                "frac_at_sampled_clock": (round(achieved_ops / (sms * FP32_LANES_PER_SM *
+                                                                 sm_med * 1e6), 4)
+                                          if sm_med else None),
                 "hbm": {"achieved": round(achieved_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
                         "frac": round(achieved_gbs / hbm_peak, 4), "peak_kind": peak_kind,
                         "bytes_per_pxch": ALGO_BYTES_PER_PXCH["u8"],
+                        "algorithmic_bytes_per_launch": ALGO_BYTES_PER_PXCH["u8"] * pxch,
                         "frac_of_nominal_7900": round(achieved_gbs / 7900.0, 4)},
                 "avg_launch_us": round(per_launch * 1e6, 3)}
 
     line = {"metric": METRIC, "value": round(value, 4), "unit": "Gpix/s", "n_gpus": world,
-            "steps": steps, "warmup": args.warmup, "ms_per_step": round(t / steps * 1e3, 5),
+            "steps": steps, "warmup": args.warmup, "ms_per_step": round(t / steps * 1e3, 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "storage": "u8", "out_mode": "2n x 2m",
-                       "beta": 2.0, "rows_per_band": rpb or "library default",
+                       "beta": 2.0, "global_batch": FRAMES_PER_STEP,
+                       "step": f"{FRAMES_PER_STEP} frames, one forward launch each",
+                       "rows_per_band": rpb or "library default",
                        "strip_width": tw or "library default (247 at this width)",
                        "autotune_ms": {f"{r}x{w}": round(v, 4) for (r, w), v in tune_ms.items()},
-                       "l2": "16 rotating input/output buffer sets (~500 MB) > 129 MB L2",
-                       "launch": "CUDA graph of 16 launches, replayed",
+                       "l2": f"{R} rotating input/output buffer sets "
+                             f"({R * 5 * H * W * C / 1e9:.2f} GB) > 129 MB L2",
+                       "launch": f"one CUDA graph of {FRAMES_PER_STEP} launches per step",
+                       "timed_s": round(t, 3),
                        "parallelism": f"replicas x{world} (no collective)"},
-            "roofline": roofline, "gpu_launches": steps, "clocks": clocks}
+            "roofline": roofline, "gpu_launches": frames, "clocks": clocks}
 
     # ---- end to end through the public API with host buffers ---------------
     # api.HostPipeline: pinned host frame in, pinned host frame out, the
@@ -424,38 +480,42 @@ def run_ours(args):
     for j in range(2 * depth):
         pipe.submit(x_pin, o_pins[j % depth])
     pipe.flush()
-    k_e2e = 200
+    k_e2e = 1  # steps of FRAMES_PER_STEP frames each
     barrier(world)
     t0 = time.perf_counter()
-    for j in range(k_e2e):
+    for j in range(k_e2e * FRAMES_PER_STEP):
         pipe.submit(x_pin, o_pins[j % depth])
     pipe.flush()
     t_e2e = max_over_ranks(world, time.perf_counter() - t0, dev)
-    line["e2e"] = {"value": round(world * k_e2e * OUT_PX / t_e2e / 1e9, 4), "unit": "Gpix/s",
-                   "h2d_bytes_per_step": int(x_host.numel()),
-                   "d2h_bytes_per_step": int(o_pins[0].numel()), "steps": k_e2e,
+    line["e2e"] = {"value": round(world * k_e2e * FRAMES_PER_STEP * OUT_PX / t_e2e / 1e9, 4),
+                   "unit": "Gpix/s",
+                   "h2d_bytes_per_step": int(x_host.numel()) * FRAMES_PER_STEP,
+                   "d2h_bytes_per_step": int(o_pins[0].numel()) * FRAMES_PER_STEP,
+                   "steps": k_e2e, "frames": k_e2e * FRAMES_PER_STEP,
                    "timer": "host wall clock, from the first submit to the last frame on the host",
                    "api": "api.HostPipeline (depth 3: H2D, zoom and D2H of neighbouring "
                           "frames overlapped)"}
-    # the same frames one at a time on one stream (no overlap), for reference
+    # frames one at a time on one stream (no overlap), for reference
     xd, od = xs[0], outs[0]
     o_pin = o_pins[0]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(50):
+    for _ in range(32):
         xd.copy_(x_pin, non_blocking=True)
         api.zoom2x_fwd(xd, params, out=od)
         o_pin.copy_(od, non_blocking=True)
     torch.cuda.synchronize()
     t_ser = max_over_ranks(world, time.perf_counter() - t0, dev)
-    line["e2e"]["serial_gpix_s"] = round(world * 50 * OUT_PX / t_ser / 1e9, 4)
+    line["e2e"]["serial_gpix_s"] = round(world * 32 * OUT_PX / t_ser / 1e9, 4)
+    del xs, outs, graph, pipe, o_pins
+    torch.cuda.empty_cache()
 
     if not args.skip_extras:
         line.update(extras(torch, np, api, scenes, dev, world, hbm_peak))
 
     if rank == 0:
         A01 = scenes.planar(img).astype(np.float64) / 255.0
-        line["cpu_baseline"] = cpu_baseline_full_frames(A01)
+        line["cpu_baseline"] = cpu_baseline(A01)
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
@@ -464,6 +524,20 @@ def run_ours(args):
 
 def extras(torch, np, api, scenes, dev, world, hbm_peak):
     out = {}
+    # the 1920x1080x3 uint8 frame -> 3840x2160 (16 rotating sets > L2)
+    hd = torch.from_numpy(scenes.planar(scenes.piecewise_smooth(1080, 1920,
+                                                                seed=scenes.seed_for(2))))
+    xs = [hd.to(dev) for _ in range(16)]
+    os_ = [torch.empty(3, 2160, 3840, dtype=torch.uint8, device=dev) for _ in range(16)]
+    t1080, _ = time_graph(torch, [lambda i=i: api.zoom2x_fwd(xs[i], out=os_[i])
+                                  for i in range(16)], 20)
+    t1080 /= 16
+    out["fwd_1080p_u8"] = {"gpix_s": round(world * 2160 * 3840 / t1080 / 1e9, 4),
+                           "us": round(t1080 * 1e6, 2),
+                           "workload": "1920x1080x3 uint8 -> 3840x2160x3 uint8, 16 rotating "
+                                       "buffer sets, graph replay"}
+    del xs, os_
+    torch.cuda.empty_cache()
     # fwd+bwd: 32x3x512x512 FP32, L2 loss against a 1024x1024 target
     xb = np.stack([scenes.planar(scenes.piecewise_smooth(512, 512, scenes.seed_for(5, i),
                                                          scale_features=True))
@@ -577,14 +651,20 @@ def extras(torch, np, api, scenes, dev, world, hbm_peak):
     o3 = torch.empty(3, 3240, 5760, dtype=torch.uint8, device=dev)
     t_rs, _ = time_graph(torch, [lambda: api.resample(hd, 3240, 5760, out=o3)], 50)
     t_z3, _ = time_graph(torch, [lambda: api.zoom_to(hd, 3240, 5760)], 20)
+    # reduction below half size per axis: the one-thread-per-output form
+    o4 = torch.empty(3, 270, 480, dtype=torch.uint8, device=dev)
+    t_dn, _ = time_graph(torch, [lambda: api.resample(hd, 270, 480, out=o4)], 50)
     opx = 3240 * 5760
     out["arbitrary_scale"] = {
         "resample_gpix_s": round(world * opx / t_rs / 1e9, 4), "resample_us": round(t_rs * 1e6, 1),
         "zoom_to_gpix_s": round(world * opx / t_z3 / 1e9, 4), "zoom_to_us": round(t_z3 * 1e6, 1),
+        "downscale_quarter_us": round(t_dn * 1e6, 2),
+        "downscale_quarter_gpix_s": round(world * 270 * 480 / t_dn / 1e9, 4),
         "workload": "1920x1080x3 uint8 -> 5760x3240x3 uint8; resample = tensor WENO alone, "
                     "zoom_to = two 2x passes on the 2n-1 grid (FP32 between) + tensor WENO "
-                    "down to 3x"}
-    del hd, o3
+                    "down to 3x; downscale_quarter = tensor WENO 1920x1080 -> 480x270 "
+                    "(one thread per output sample)"}
+    del hd, o3, o4
     torch.cuda.empty_cache()
 
     # inverse problem: recover 256x256x3 from its 512x512 zoom, 200 Adam steps
@@ -631,7 +711,20 @@ def run_case(args):
     import torch
     from paper_2312_00229_gb300 import api, scenes
     dev = torch.device("cuda")
-    if args.case == "resample3x":
+    if args.case == "fwd4k":
+        frame = torch.from_numpy(scenes.planar(scenes.piecewise_smooth(H, W,
+                                                                       seed=scenes.seed_for(4))))
+        xs = [frame.to(dev) for _ in range(ROTATING_SETS)]
+        outs = [torch.empty(C, 2 * H, 2 * W, dtype=torch.uint8, device=dev)
+                for _ in range(ROTATING_SETS)]
+        it = [0]
+
+        def step():
+            i = it[0] % ROTATING_SETS
+            it[0] += 1
+            api.zoom2x_fwd(xs[i], out=outs[i], rows_per_tile=0)
+        work = f"{W}x{H}x{C} uint8 -> {2 * W}x{2 * H}, {ROTATING_SETS} rotating buffer sets"
+    elif args.case == "resample3x":
         hd = torch.from_numpy(scenes.planar(scenes.piecewise_smooth(
             1080, 1920, seed=scenes.seed_for(2)))).to(dev)
         o = torch.empty(3, 3240, 5760, dtype=torch.uint8, device=dev)

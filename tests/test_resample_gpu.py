@@ -214,3 +214,14 @@ def test_resample_fp32_with_data_bound():
     b = api.resample(x, 130, 201)
     torch.cuda.synchronize()
     assert (a - b).abs().max().item() <= 4e-6
+
+
+@pytest.mark.parametrize("dt", ["u8", "f16", "f32"])
+def test_resample_large_reduction_one_thread_per_output(dt):
+    """Reductions below half size per axis take the one-thread-per-output
+    form (a 4x4 window read per sample); parity on storage types."""
+    img = scenes.piecewise_smooth(400, 600, seed=scenes.seed_for(6, 3), scale_features=True)
+    A = scenes.planar(img).astype(np.float64) / 255.0
+    for dst in [(90, 130), (100, 290), (190, 140)]:
+        out, ref = _resample(A, *dst, dt, dt)
+        parity.compare(out, ref, dt)
