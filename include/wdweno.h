@@ -122,20 +122,18 @@ int weno_zoom2x_fwd(const weno_image* in, weno_dtype in_t, const weno_image* out
  *   grad_out  : FP32, shaped like the forward output for p->out_mode
  *   grad_in   : FP32, shaped like x; overwritten (not accumulated)
  *   workspace : device scratch of >= weno_zoom2x_bwd_workspace_bytes(x)
- *               bytes, 16-byte aligned; no initialisation needed; it holds
- *               the clamp-extended input, the recomputed indicators and
- *               phase-1 values, the per-point adjoints and the per-stencil
- *               node coefficients
- * Returns WENO_OK, WENO_EINVAL, WENO_EWORKSPACE, WENO_ECUDA, or WENO_ERANGE
- * when a plane extended by 7 cells per side has 2^31 cells or more. */
+ *               bytes, 16-byte aligned; no initialisation needed; it carries
+ *               the adjoints of the phase-1 values and the partial adjoint
+ *               of the input samples from the phase-2 sweep to the phase-1
+ *               sweep (two fused kernels, everything else stays on chip)
+ * Returns WENO_OK, WENO_EINVAL, WENO_EWORKSPACE or WENO_ECUDA. */
 int weno_zoom2x_bwd(const weno_image* x, const weno_image* grad_out,
                     const weno_image* grad_in, const weno_params* p, void* workspace,
                     size_t workspace_bytes, void* stream);
 
 /* Scratch bytes weno_zoom2x_bwd needs for an input shaped like `x`
- * (55 FP32 values per cell of the image extended by 7 cells per side, per
- * channel, the cell count rounded up to a multiple of 4).  Returns 0 for a
- * malformed descriptor. */
+ * (2 FP32 values per cell of the image extended by 2 cells per side, per
+ * channel).  Returns 0 for a malformed descriptor. */
 size_t weno_zoom2x_bwd_workspace_bytes(const weno_image* x);
 
 /* Workspace needed by weno_zoom2x_batched for `count` images (bytes). */

@@ -349,10 +349,8 @@ int weno_zoom2x_bwd(const weno_image* x, const weno_image* grad_out, const weno_
   if (!workspace || workspace_bytes < bwd_workspace_bytes(x->height, x->width, x->channels) ||
       reinterpret_cast<uintptr_t>(workspace) % 16 != 0)
     return WENO_EWORKSPACE;
-  if ((x->height + 2 * BWD_GHOST + 7) / 8 > 65535) return WENO_ERANGE;
-  // the adjoint kernels index a plane's cells with 32-bit integers
-  if ((x->height + 2 * BWD_GHOST) * (x->width + 2 * BWD_GHOST) + 3 >= (int64_t(1) << 31))
-    return WENO_ERANGE;
+  // (image_ok bounds the output's sides below 2^31, so the kernels' 32-bit
+  // rows and columns and the one grid layer of CTAs per channel fit)
   MethodConsts k;
   int bmode;
   if (!fold_consts(p, &k, &bmode)) return WENO_EINVAL;

@@ -13,172 +13,150 @@
 //     N0: 3/8 p_bar + (-2 g + 2 kappa^2 s) SI_bar
 //     N1: 3/4 p_bar + ( 2 g - 4 kappa^2 s) SI_bar
 //     N2: -1/8 p_bar + 2 kappa^2 s SI_bar .
-// Every quantity is computed once per cell of a grid extended by BWD_GHOST
-// cells per side (clamp-to-edge) and kept in the workspace; scatters are
-// written as gathers over these arrays (no atomics):
-//   k_xsi      phase-1 indicators (4 directions) of every x point, and the
-//              clamp-extended copy of the input that the later kernels read
-//              their stencil nodes from (no clamping or 64-bit indexing)
-//   k_xval     phase-1 values X
-//   k_psi      phase-2 indicators of every E and S point
-//   k_padj     p_bar, D_bar of the "+" points that receive an output gradient
-//   k_coef<T>  per stencil and node role, the coefficient above
-//   k_gather2_xadj  X_bar (plus the x-point output gradient) and A_bar from
-//              phase 2 (plus the sample-point output gradient), then the
-//              x point's p_bar, D_bar from that X_bar
-//   k_gather1  A_bar += phase-1 contributions
-//   k_fold     grad_in = A_bar summed over each pixel's clamp preimage
+//
+// Two row-sweep kernels, each CTA one plane x one strip of columns x one band
+// of rows, sweeping its band top to bottom one coarse row per step with one
+// barrier per step; every intermediate lives in shared-memory rings of
+// recent rows (slot = row mod ring depth), and a stage at step s works on
+// row s - L for its own lag L, reading only rows written in earlier steps.
+//
+//   k_bwd_plus   recomputes the forward pass (phase-1 indicators and values,
+//                phase-2 indicators) and runs the phase-2 adjoint: p_bar,
+//                D_bar of every E and S point, their SI_bar and the node
+//                coefficients, gathered onto the x points (X_bar, plus the
+//                x-point output gradient) and onto the input samples (plus
+//                the sample-point output gradient).  Writes X_bar and that
+//                partial A_bar on the grid extended by 2 cells per side.
+//   k_bwd_cross  recomputes the phase-1 indicators, runs the phase-1 adjoint
+//                from X_bar, gathers the node coefficients onto the samples,
+//                adds the partial A_bar and folds the clamp-to-edge
+//                extension back onto the edge pixels (its adjoint).
+// Scatters are gathers: a contribution to a thread's own column is added to
+// a short register ring of row accumulators, contributions to other columns
+// are published per row in shared memory and gathered one step later.
 #include "wd_bwd.h"
 
 namespace wdweno {
 
 namespace {
 
-constexpr int G = BWD_GHOST;
-// A 32 x 8 block covers 32 columns and R x 8 rows of cells: a thread takes R
-// cells of its column, 8 rows apart.  Three light kernels take four cells and
-// the x-stencil coefficients two, so a block's start-up is spread over more
-// work; the others take one, which keeps their register count (and
-// occupancy) down (chosen by measurement).
-constexpr int BWD_BY = 8;
-constexpr int R_XSI = 4, R_XVAL = 4, R_PSI = 1, R_PADJ = 1, R_COEF2 = 1, R_G2 = 1, R_COEF1 = 2,
-              R_G1 = 1, R_FOLD = 4;
+// ---- shared-memory rings ------------------------------------------------------
+constexpr int PAD = 2;  // ring columns before / after the CTA's threads
 
-// Workspace layout per plane (NE x ME cells, the cell count padded to a
-// multiple of 4): seven float4 planes for the four-direction vectors, then
-// scalar planes.
-enum VGroup {
-  G_XSI = 0,  // phase-1 SIs
-  G_ESI = 1,  // E-point SIs
-  G_SSI = 2,  // S-point SIs
-  G_EP = 3,   // E p_bar   (the phase-1 adjoint reuses G_EP, G_ED for x points)
-  G_ED = 4,   // E D_bar
-  G_SP = 5,   // S p_bar
-  G_SD = 6,   // S D_bar
-  G_N = 7
-};
-enum Slot {
-  S_X = 0,     // phase-1 values
-  S_AB = 1,    // A_bar on the extended grid
-  S_ECO = 2,   // 12: E coefficients, index k*3 + t   (phase 1 reuses for x)
-  S_SCO = 14,  // 12: S coefficients
-  S_A = 26,    // the input, clamp-extended to the work grid
-  S_N = 27
-};
-static_assert(4 * G_N + S_N == BWD_ARRAYS, "workspace slot count");
+// k_bwd_plus: thread t owns column c = b0 - HL1 + t of a strip whose outputs
+// are columns [b0, b0 + NT - HL1 - HR1) of the extended grid.
+constexpr int NT1 = 128, HL1 = 6, HR1 = 7, TW1 = NT1 - HL1 - HR1;
+// k_bwd_cross: the strip's outputs are image columns [b0, b0 + TW2) plus,
+// at the image edges, the ghost columns folded onto them.
+constexpr int NT2 = 128, HL2 = 10, HR2 = 10, TW2 = NT2 - HL2 - HR2;
+constexpr int GA = 5;  // ghost rows / columns of A_bar (nonzero up to 4)
 
-// Point types: 0 = x point X(a,b) (fine (2a+1, 2b+1)), 1 = E point
-// (fine (2a, 2b+1)), 2 = S point (fine (2a+1, 2b)).  For each type and
-// direction k the nodes N0, N1, N2 sit at (a, b) + off on the lattice of input
-// samples (lattice 0) or of x points (lattice 1).
-// x: k = 0 (1,1), 1 (-1,-1), 2 (1,-1), 3 (-1,1)
-// E, S: k = 0 (0,1), 1 (0,-1), 2 (1,0), 3 (-1,0)
-// Compile-time tables: every call site passes literal or unrolled indices,
-// so the lookups fold into immediates.
-__device__ __forceinline__ int off_of(int type, int k, int t, int d) {
-  constexpr int tab[3][4][3][2] = {
-      {{{0, 0}, {1, 1}, {2, 2}}, {{1, 1}, {0, 0}, {-1, -1}},
-       {{0, 1}, {1, 0}, {2, -1}}, {{1, 0}, {0, 1}, {-1, 2}}},
-      {{{0, 0}, {0, 1}, {0, 2}}, {{0, 1}, {0, 0}, {0, -1}},
-       {{-1, 0}, {0, 0}, {1, 0}}, {{0, 0}, {-1, 0}, {-2, 0}}},
-      {{{0, -1}, {0, 0}, {0, 1}}, {{0, 0}, {0, -1}, {0, -2}},
-       {{0, 0}, {1, 0}, {2, 0}}, {{1, 0}, {0, 0}, {-1, 0}}}};
-  return tab[type][k][t][d];
-}
-__device__ __forceinline__ int lattice_of(int type, int k) {
-  constexpr int tab[3][4] = {{0, 0, 0, 0}, {0, 0, 1, 1}, {1, 1, 0, 0}};
-  return tab[type][k];
-}
-
-struct Ctx {
-  const float* x;  // input plane
-  int n, m;
-  int64_t sh, sw;
-  float* ws;       // workspace plane
-  int NE, ME;
-  int64_t plane_cells;  // NE * ME rounded up to a multiple of 4 (< 2^31, checked on the host)
-  float w, kap1, kap2, eps1, eps2, beta;
+template <int NT>
+struct RingsPlus {
+  static constexpr int W = NT + 2 * PAD;
+  float A[16][W];     // input rows, slot = row & 15
+  float X[16][W];     // phase-1 values
+  float4 SIX[4][W];   // phase-1 indicators (4 directions)
+  float4 SIE[4][W];   // E-point indicators
+  float4 SIS[4][W];   // S-point indicators
+  float4 DE[4][W];    // E D_bar
+  float4 DS[4][W];    // S D_bar
+  float4 EH[2][W];    // E along-row stencils: node contributions to columns c-1..c+2
+  float4 SH[4][W];    // S along-row stencils: contributions to x columns c-2..c+1
 };
 
-__device__ __forceinline__ int clampi(int v, int lo, int hi) {
-  return v < lo ? lo : (v > hi ? hi : v);
+template <int NT>
+struct RingsCross {
+  static constexpr int W = NT + 2 * PAD;
+  float A[16][W];
+  float4 SIX[4][W];
+  float4 PX[4][W];    // x p_bar
+  float4 DX[4][W];    // x D_bar
+  float2 C1[2][W];    // contributions to column c+1: rows a, a+1
+  float2 C2[2][W];    // to column c+2: rows a+2, a-1
+  float2 CM[2][W];    // to column c-1: rows a-1, a+2
+  float AF[2][W];     // row-folded A_bar of the row emitted in the previous step
+};
+
+// ---- the method's per-point quantities ---------------------------------------
+struct Sten {
+  float g[4], s[4];  // N1 - N0 and N0 - 2 N1 + N2 per direction
+  float M[2];        // N0 + N1 of the direction pairs (0,1) and (2,3)
+};
+
+__device__ __forceinline__ void sten(float n0, float n1, float n2, float& g, float& s) {
+  g = n1 - n0;
+  s = fmaf(-2.f, n1, n0 + n2);
 }
 
-__device__ __forceinline__ float Ahat(const Ctx& c, int i, int j) {
-  return __ldg(c.x + (int64_t)clampi(i, 0, c.n - 1) * c.sh + (int64_t)clampi(j, 0, c.m - 1) * c.sw);
+// x point X(a,b) (fine (2a+1, 2b+1)).  Directions: 0 (1,1): A(a,b),
+// A(a+1,b+1), A(a+2,b+2); 1 (-1,-1): A(a+1,b+1), A(a,b), A(a-1,b-1);
+// 2 (1,-1): A(a,b+1), A(a+1,b), A(a+2,b-1); 3 (-1,1): A(a+1,b), A(a,b+1),
+// A(a-1,b+2).  am1..a2: rows a-1 .. a+2 at column b.
+__device__ __forceinline__ Sten sten_x(const float* am1, const float* a0, const float* a1,
+                                       const float* a2) {
+  Sten q;
+  sten(a0[0], a1[1], a2[2], q.g[0], q.s[0]);
+  sten(a1[1], a0[0], am1[-1], q.g[1], q.s[1]);
+  sten(a0[1], a1[0], a2[-1], q.g[2], q.s[2]);
+  sten(a1[0], a0[1], am1[2], q.g[3], q.s[3]);
+  q.M[0] = a0[0] + a1[1];
+  q.M[1] = a0[1] + a1[0];
+  return q;
 }
 
-__device__ __forceinline__ bool in_ext(const Ctx& c, int I, int J) {
-  return I >= -G && I < c.n + G && J >= -G && J < c.m + G;
+// E point E(r,c) (fine (2r, 2c+1)).  0 (0,1): A(r,c), A(r,c+1), A(r,c+2);
+// 1 (0,-1): A(r,c+1), A(r,c), A(r,c-1); 2 (1,0): X(r-1,c), X(r,c), X(r+1,c);
+// 3 (-1,0): X(r,c), X(r-1,c), X(r-2,c).  ar: row r of A at column c;
+// xm2..x1: rows r-2 .. r+1 of X at column c.
+__device__ __forceinline__ Sten sten_e(const float* ar, float xm2, float xm1, float x0,
+                                       float x1) {
+  Sten q;
+  sten(ar[0], ar[1], ar[2], q.g[0], q.s[0]);
+  sten(ar[1], ar[0], ar[-1], q.g[1], q.s[1]);
+  sten(xm1, x0, x1, q.g[2], q.s[2]);
+  sten(x0, xm1, xm2, q.g[3], q.s[3]);
+  q.M[0] = ar[0] + ar[1];
+  q.M[1] = xm1 + x0;
+  return q;
 }
 
-// 32-bit: the cell count of a plane is below 2^31.
-__device__ __forceinline__ int cell(const Ctx& c, int I, int J) {
-  return (I + G) * c.ME + (J + G);
+// S point S(r,c) (fine (2r+1, 2c)).  0 (0,1): X(r,c-1), X(r,c), X(r,c+1);
+// 1 (0,-1): X(r,c), X(r,c-1), X(r,c-2); 2 (1,0): A(r,c), A(r+1,c), A(r+2,c);
+// 3 (-1,0): A(r+1,c), A(r,c), A(r-1,c).  xr: row r of X at column c;
+// am1..a2: rows r-1 .. r+2 of A at column c.
+__device__ __forceinline__ Sten sten_s(const float* xr, float am1, float a0, float a1,
+                                       float a2) {
+  Sten q;
+  sten(xr[-1], xr[0], xr[1], q.g[0], q.s[0]);
+  sten(xr[0], xr[-1], xr[-2], q.g[1], q.s[1]);
+  sten(a0, a1, a2, q.g[2], q.s[2]);
+  sten(a1, a0, am1, q.g[3], q.s[3]);
+  q.M[0] = xr[-1] + xr[0];
+  q.M[1] = a0 + a1;
+  return q;
 }
 
-__device__ __forceinline__ float& W(const Ctx& c, int slot, int I, int J) {
-  return c.ws[(4 * G_N + slot) * c.plane_cells + cell(c, I, J)];
-}
-
-// Workspace value, 0 outside the extended grid.
-__device__ __forceinline__ float W0(const Ctx& c, int slot, int I, int J) {
-  return in_ext(c, I, J) ? W(c, slot, I, J) : 0.f;
-}
-
-__device__ __forceinline__ float4& V(const Ctx& c, int g, int I, int J) {
-  return reinterpret_cast<float4*>(c.ws)[g * c.plane_cells + cell(c, I, J)];
-}
-
-__device__ __forceinline__ float4 V0(const Ctx& c, int g, int I, int J) {
-  return in_ext(c, I, J) ? V(c, g, I, J) : make_float4(0.f, 0.f, 0.f, 0.f);
+__device__ __forceinline__ float4 indicators(const Sten& q, float kap, float eps) {
+  float si[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float ks = kap * q.s[k];
+    si[k] = fmaf(q.g[k], q.g[k], fmaf(ks, ks, eps));
+  }
+  return make_float4(si[0], si[1], si[2], si[3]);
 }
 
 __device__ __forceinline__ float comp(const float4& v, int d) {
   return d == 0 ? v.x : (d == 1 ? v.y : (d == 2 ? v.z : v.w));
 }
 
-__device__ __forceinline__ float4 f4(const float a[4]) {
-  return make_float4(a[0], a[1], a[2], a[3]);
-}
-
-// Stencil node of a point: input samples from the clamp-extended copy (or,
-// with COPY = false, clamped reads of the input itself), x points from the
-// phase-1 values.  Every caller's nodes lie inside the work grid.
-template <bool COPY = true>
-__device__ __forceinline__ float node(const Ctx& c, int type, int k, int t, int a, int b) {
-  const int i = a + off_of(type, k, t, 0), j = b + off_of(type, k, t, 1);
-  if (lattice_of(type, k) == 1) return W(c, S_X, i, j);
-  return COPY ? W(c, S_A, i, j) : Ahat(c, i, j);
-}
-
-struct Pt {
-  float p[4];   // interpolants
-  float si[4];  // indicators (eps' included)
-  float M[2];   // N0 + N1 of the pairs (0,1) and (2,3)
-  float s[4];   // second differences
-};
-
-template <bool COPY = true>
-__device__ __forceinline__ Pt eval_pt(const Ctx& c, int type, int a, int b) {
-  Pt q;
-  const float kap = type == 0 ? c.kap1 : c.kap2;
-  const float eps = type == 0 ? c.eps1 : c.eps2;
+// D_k = own_k + w (n0 + n1 + n2 + n3)_k
+__device__ __forceinline__ void smooth(const float4& own, const float4& n0, const float4& n1,
+                                       const float4& n2, const float4& n3, float w, float D[4]) {
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const float n0 = node<COPY>(c, type, k, 0, a, b);
-    const float n1 = node<COPY>(c, type, k, 1, a, b);
-    const float n2 = node<COPY>(c, type, k, 2, a, b);
-    const float g = n1 - n0;
-    const float s = fmaf(-2.f, n1, n0 + n2);
-    const float ks = kap * s;
-    q.si[k] = fmaf(g, g, fmaf(ks, ks, eps));
-    q.s[k] = s;
-    q.p[k] = fmaf(-0.125f, s, 0.5f * (n0 + n1));
-    if (k == 0) q.M[0] = n0 + n1;
-    if (k == 2) q.M[1] = n0 + n1;
-  }
-  return q;
+  for (int d = 0; d < 4; ++d)
+    D[d] = fmaf(w, (comp(n0, d) + comp(n1, d)) + (comp(n2, d) + comp(n3, d)), comp(own, d));
 }
 
 // Normalised weights omega_k from D_k (Eqs. alpha, IzrazOmega2d).
@@ -202,359 +180,472 @@ __device__ __forceinline__ void weights(const float D[4], float beta, float om[4
   for (int k = 0; k < 4; ++k) om[k] = al[k] * inv;
 }
 
-// p_bar, D_bar of one blend point given its D and interpolant data.
+// p_k = (N0 + N1)/2 - s_k/8 (Eq. p)
+__device__ __forceinline__ float interp(const Sten& q, int k) {
+  return fmaf(-0.125f, q.s[k], 0.5f * q.M[k >> 1]);
+}
+
+// p_bar, D_bar of one blend point given its D and stencil data.
 template <int BMODE>
-__device__ __forceinline__ void point_adjoint(const Pt& q, const float D[4], float beta, float ub,
-                                              float pb[4], float db[4]) {
-  float om[4];
+__device__ __forceinline__ void point_adjoint(const Sten& q, const float D[4], float beta,
+                                              float ub, float4& pb4, float4& db4) {
+  float om[4], pb[4], db[4];
   weights<BMODE>(D, beta, om);
-  // p_k - u = sum_l omega_l (p_k - p_l), each difference formed from the
-  // stencil data to avoid cancelling two O(1) values.
+  // p_k - u from differences of the stencil data, so that no two O(1)
+  // values cancel: d_k = p_k - p_0 = (M_k - M_0)/2 - (s_k - s_0)/8 and
+  // u - p_0 = sum_l omega_l d_l, so p_k - u = d_k - sum_l omega_l d_l.
+  const float hM = 0.5f * (q.M[1] - q.M[0]);
+  const float d1 = -0.125f * (q.s[1] - q.s[0]);
+  const float d2 = fmaf(-0.125f, q.s[2] - q.s[0], hM);
+  const float d3 = fmaf(-0.125f, q.s[3] - q.s[0], hM);
+  const float v = fmaf(om[1], d1, fmaf(om[2], d2, om[3] * d3));
+  const float pu[4] = {-v, d1 - v, d2 - v, d3 - v};
+  const float ubb = -ub * beta;
 #pragma unroll
   for (int kk = 0; kk < 4; ++kk) {
-    float acc = 0.f;
-#pragma unroll
-    for (int l = 0; l < 4; ++l) {
-      const float dM = (kk >> 1) == (l >> 1) ? 0.f : q.M[kk >> 1] - q.M[l >> 1];
-      acc = fmaf(om[l], fmaf(0.5f, dM, -0.125f * (q.s[kk] - q.s[l])), acc);
-    }
     pb[kk] = ub * om[kk];
-    db[kk] = BMODE == B0 ? 0.f : -ub * beta * om[kk] * acc * rcp_approx(D[kk]);
+    db[kk] = BMODE == B0 ? 0.f : ubb * om[kk] * pu[kk] * rcp_approx(D[kk]);
+  }
+  pb4 = make_float4(pb[0], pb[1], pb[2], pb[3]);
+  db4 = make_float4(db[0], db[1], db[2], db[3]);
+}
+
+// Node coefficients (N0, N1, N2) of the four stencils of a point.
+__device__ __forceinline__ void node_coefs(const Sten& q, const float4& pb, const float sb[4],
+                                           float k2, float c[4][3]) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float pbar = comp(pb, k), sbar = sb[k];
+    const float g2 = 2.f * q.g[k] * sbar, s2 = 2.f * k2 * q.s[k] * sbar;
+    c[k][0] = fmaf(0.375f, pbar, s2 - g2);
+    c[k][1] = fmaf(0.75f, pbar, fmaf(-2.f, s2, g2));
+    c[k][2] = fmaf(-0.125f, pbar, s2);
   }
 }
 
-// The thread's column J and first row I0; it takes rows I0 + r BWD_BY,
-// r < R, that lie on the extended grid.
-template <int R>
-__device__ __forceinline__ bool setup(const BwdArgs& a, const MethodConsts& k, Ctx& c, int& I0,
-                                      int& J) {
+__device__ __forceinline__ int clampi(int v, int lo, int hi) {
+  return v < lo ? lo : (v > hi ? hi : v);
+}
+
+// Extended-grid planes of the workspace: X_bar and the partial A_bar,
+// (n + 2 BWD_GHOST) x (m + 2 BWD_GHOST) floats each, per plane.
+struct WsPlane {
+  float* xb;
+  float* ab;
+  int64_t ld;  // row stride
+  __device__ __forceinline__ int64_t idx(int r, int c) const {
+    return (int64_t)(r + BWD_GHOST) * ld + (c + BWD_GHOST);
+  }
+};
+
+__device__ __forceinline__ WsPlane ws_plane(const BwdArgs& a, int64_t plane) {
+  WsPlane w;
+  w.ld = a.m + 2 * BWD_GHOST;
+  const int64_t cells = (a.n + 2 * BWD_GHOST) * w.ld;
+  w.xb = a.ws + plane * 2 * cells;
+  w.ab = w.xb + cells;
+  return w;
+}
+
+// ---- k_bwd_plus ----------------------------------------------------------------
+// Output-gradient column of a thread (fine column Q, element pointer at row
+// 0), read row by row.
+struct GCol {
+  const float* p;
+  int64_t sh;
+  int orows;
+  bool ok;
+  __device__ __forceinline__ float at(int P) const {
+    return (ok && P >= 0 && P < orows) ? __ldg(p + (int64_t)P * sh) : 0.f;
+  }
+};
+
+__device__ __forceinline__ GCol gcol(const BwdArgs& a, int64_t plane, int64_t Q) {
+  GCol g;
+  g.ok = Q >= 0 && Q < a.ocols;
+  g.p = a.gout + plane * a.g_sc + (g.ok ? Q : 0) * a.g_sw;
+  g.sh = a.g_sh;
+  g.orows = (int)a.orows;
+  return g;
+}
+
+// Lags (row = s - L at step s): input row 0, x indicators 3, x values 5,
+// "+" indicators 7, "+" adjoints 9, "+" coefficients 11; the partial A_bar of
+// row s - 12 and X_bar of row s - 13 are complete at the end of step s.
+template <int BMODE>
+__global__ void __launch_bounds__(NT1, 3) k_bwd_plus(BwdArgs a, MethodConsts k, int rows) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  RingsPlus<NT1>& R = *reinterpret_cast<RingsPlus<NT1>*>(smem);
+  const int t = threadIdx.x;
   const int64_t plane = blockIdx.z;
-  c.n = (int)a.n; c.m = (int)a.m; c.sh = a.x_sh; c.sw = a.x_sw;
-  c.x = a.x + plane * a.x_sc;
-  c.NE = c.n + 2 * G; c.ME = c.m + 2 * G;
-  c.plane_cells = ((int64_t)c.NE * c.ME + 3) & ~int64_t(3);
-  c.ws = a.ws + plane * (int64_t)BWD_ARRAYS * c.plane_cells;
-  c.w = k.w; c.kap1 = k.kappa1; c.kap2 = k.kappa2; c.eps1 = k.eps1; c.eps2 = k.eps2;
-  c.beta = k.beta;
-  J = (int)(blockIdx.x * blockDim.x + threadIdx.x) - G;
-  I0 = (int)(blockIdx.y * (BWD_BY * R) + threadIdx.y) - G;
-  return J < c.m + G;
-}
+  const int n = (int)a.n, m = (int)a.m;
+  const int b0 = -BWD_GHOST + (int)blockIdx.x * TW1;
+  const int b1 = min(b0 + TW1, m + BWD_GHOST);
+  const int c = b0 - HL1 + t;
+  const int a0 = -BWD_GHOST + (int)blockIdx.y * rows;
+  const int a1 = min(a0 + rows, n + BWD_GHOST);
+  const float* xin = a.x + plane * a.x_sc + (int64_t)clampi(c, 0, m - 1) * a.x_sw;
+  const WsPlane ws = ws_plane(a, plane);
+  const bool col_out = c >= b0 && c < b1;
+  // fine column 2c + 1 (E and x points) and 2c (S points and samples)
+  const GCol godd = gcol(a, plane, 2 * (int64_t)c + 1), gevn = gcol(a, plane, 2 * (int64_t)c);
+  const float w = k.w;
+  const float k2 = k.kappa2 * k.kappa2;
 
-__device__ __forceinline__ float gout_at(const BwdArgs& a, int64_t plane, int64_t P, int64_t Q) {
-  if (P < 0 || Q < 0 || P >= a.orows || Q >= a.ocols) return 0.f;
-  return __ldg(a.gout + plane * a.g_sc + P * a.g_sh + Q * a.g_sw);
-}
-
-// Region where x values, their indicators and the "+" indicators are
-// needed: rows/columns -4 .. n+3 (x values feed "+" stencils up to 3 fine
-// steps away from the output quads, whose D reads one more ring).
-__device__ __forceinline__ bool in_core(const Ctx& c, int I, int J) {
-  return I >= -5 && I < c.n + 5 && J >= -5 && J < c.m + 5;
-}
-
-// ---- forward recompute ------------------------------------------------------
-__global__ void k_xsi(BwdArgs a, MethodConsts k) {
-  Ctx c; int I0, J;
-  if (!setup<R_XSI>(a, k, c, I0, J)) return;
-  for (int r = 0; r < R_XSI; ++r) {
-    const int I = I0 + r * BWD_BY;
-    if (I >= c.n + G) break;
-    float si[4] = {0.f, 0.f, 0.f, 0.f};
-    if (in_core(c, I, J)) {
-      const Pt q = eval_pt<false>(c, 0, I, J);
-  #pragma unroll
-      for (int d = 0; d < 4; ++d) si[d] = q.si[d];
-    }
-    V(c, G_XSI, I, J) = f4(si);
-    W(c, S_A, I, J) = Ahat(c, I, J);
+  {
+    float* z = reinterpret_cast<float*>(smem);
+    for (int i = t; i < (int)(sizeof(RingsPlus<NT1>) / sizeof(float)); i += NT1) z[i] = 0.f;
   }
-}
+  const int u = t + PAD;  // this thread's column in the rings
+  const int s_begin = a0 - 6, s_end = a1 - 1 + 13;
+  float pf = __ldg(xin + (int64_t)clampi(s_begin, 0, n - 1) * a.x_sh);
+  float pf2 = __ldg(xin + (int64_t)clampi(s_begin + 1, 0, n - 1) * a.x_sh);
+  // output gradients of the next step's rows, loaded one step ahead
+  float ue = godd.at(2 * (s_begin - 9)), us = gevn.at(2 * (s_begin - 9) + 1);
+  float gx = godd.at(2 * (s_begin - 13) + 1), ga = gevn.at(2 * (s_begin - 12));
+  // p_bar of the "+" points of rows s-10 (1) and s-11 (2), kept by the thread
+  float4 pe1 = make_float4(0.f, 0.f, 0.f, 0.f), pe2 = pe1, ps1 = pe1, ps2 = pe1;
+  // own-column row accumulators: X_bar rows r-2 .. r+1, A_bar rows r-1 .. r+2
+  // (r = the coefficient stage's row)
+  float xacc[4] = {0.f, 0.f, 0.f, 0.f}, aacc[4] = {0.f, 0.f, 0.f, 0.f};
 
-template <int BMODE>
-__device__ __forceinline__ void d_x(const Ctx& c, int I, int J, const float si[4], float D[4]) {
-  const float4 u = V0(c, G_XSI, I - 1, J), v = V0(c, G_XSI, I + 1, J);
-  const float4 l = V0(c, G_XSI, I, J - 1), r = V0(c, G_XSI, I, J + 1);
-#pragma unroll
-  for (int d = 0; d < 4; ++d)
-    D[d] = fmaf(c.w, comp(u, d) + comp(v, d) + comp(l, d) + comp(r, d), si[d]);
-}
+  for (int s = s_begin; s <= s_end; ++s) {
+    const float cur = pf;
+    pf = pf2;
+    pf2 = __ldg(xin + (int64_t)clampi(s + 2, 0, n - 1) * a.x_sh);
+    const float ue_s = ue, us_s = us, gx_s = gx, ga_s = ga;
+    ue = godd.at(2 * (s - 8));
+    us = gevn.at(2 * (s - 8) + 1);
+    gx = godd.at(2 * (s - 12) + 1);
+    ga = gevn.at(2 * (s - 11));
+    __syncthreads();
+    R.A[s & 15][u] = cur;
 
-template <int BMODE>
-__global__ void k_xval(BwdArgs a, MethodConsts k) {
-  Ctx c; int I0, J;
-  if (!setup<R_XVAL>(a, k, c, I0, J)) return;
-  for (int r = 0; r < R_XVAL; ++r) {
-    const int I = I0 + r * BWD_BY;
-    if (I >= c.n + G) break;
-    float v = 0.f;
-    if (I >= -4 && I < c.n + 4 && J >= -4 && J < c.m + 4) {
-      const Pt q = eval_pt(c, 0, I, J);
+    // ---- x indicators, row s-3 ----
+    {
+      const int ra = s - 3;
+      const Sten q = sten_x(R.A[(ra - 1) & 15] + u, R.A[ra & 15] + u, R.A[(ra + 1) & 15] + u,
+                            R.A[(ra + 2) & 15] + u);
+      R.SIX[ra & 3][u] = indicators(q, k.kappa1, k.eps1);
+    }
+    // ---- x values, row s-5 ----
+    {
+      const int ra = s - 5;
       float D[4], om[4];
-      d_x<BMODE>(c, I, J, q.si, D);
-      weights<BMODE>(D, c.beta, om);
-      v = om[0] * q.p[0] + om[1] * q.p[1] + om[2] * q.p[2] + om[3] * q.p[3];
+      smooth(R.SIX[ra & 3][u], R.SIX[(ra - 1) & 3][u], R.SIX[(ra + 1) & 3][u],
+             R.SIX[ra & 3][u - 1], R.SIX[ra & 3][u + 1], w, D);
+      weights<BMODE>(D, k.beta, om);
+      const Sten q = sten_x(R.A[(ra - 1) & 15] + u, R.A[ra & 15] + u, R.A[(ra + 1) & 15] + u,
+                            R.A[(ra + 2) & 15] + u);
+      float x = 0.f;
+#pragma unroll
+      for (int d = 0; d < 4; ++d) x = fmaf(om[d], interp(q, d), x);
+      R.X[ra & 15][u] = x;
     }
-    W(c, S_X, I, J) = v;
-  }
-}
-
-__global__ void k_psi(BwdArgs a, MethodConsts k) {
-  Ctx c; int I0, J;
-  if (!setup<R_PSI>(a, k, c, I0, J)) return;
-  for (int r = 0; r < R_PSI; ++r) {
-    const int I = I0 + r * BWD_BY;
-    if (I >= c.n + G) break;
-    float e[4] = {0.f, 0.f, 0.f, 0.f}, s[4] = {0.f, 0.f, 0.f, 0.f};
-    if (I >= -2 && I < c.n + 2 && J >= -2 && J < c.m + 2) {
-      const Pt qe = eval_pt(c, 1, I, J);
-      const Pt qs = eval_pt(c, 2, I, J);
-  #pragma unroll
-      for (int d = 0; d < 4; ++d) { e[d] = qe.si[d]; s[d] = qs.si[d]; }
+    // ---- "+" indicators, row s-7 ----
+    {
+      const int r = s - 7;
+      const Sten qe = sten_e(R.A[r & 15] + u, R.X[(r - 2) & 15][u], R.X[(r - 1) & 15][u],
+                             R.X[r & 15][u], R.X[(r + 1) & 15][u]);
+      R.SIE[r & 3][u] = indicators(qe, k.kappa2, k.eps2);
+      const Sten qs = sten_s(R.X[r & 15] + u, R.A[(r - 1) & 15][u], R.A[r & 15][u],
+                             R.A[(r + 1) & 15][u], R.A[(r + 2) & 15][u]);
+      R.SIS[r & 3][u] = indicators(qs, k.kappa2, k.eps2);
     }
-    V(c, G_ESI, I, J) = f4(e);
-    V(c, G_SSI, I, J) = f4(s);
-  }
-}
-
-// ---- phase-2 adjoint ------------------------------------------------------------
-template <int BMODE>
-__global__ void k_padj(BwdArgs a, MethodConsts k) {
-  Ctx c; int I0, J;
-  if (!setup<R_PADJ>(a, k, c, I0, J)) return;
-  for (int r = 0; r < R_PADJ; ++r) {
-    const int I = I0 + r * BWD_BY;
-    if (I >= c.n + G) break;
-    float pE[4] = {0.f, 0.f, 0.f, 0.f}, dE[4] = {0.f, 0.f, 0.f, 0.f};
-    float pS[4] = {0.f, 0.f, 0.f, 0.f}, dS[4] = {0.f, 0.f, 0.f, 0.f};
-    if (I >= 0 && I < c.n && J >= 0 && J < c.m) {
-      const int64_t plane = blockIdx.z;
-      const float uE = gout_at(a, plane, 2 * (int64_t)I, 2 * (int64_t)J + 1);
-      const float uS = gout_at(a, plane, 2 * (int64_t)I + 1, 2 * (int64_t)J);
-      if (uE != 0.f) {
-        // E(a,b): D reads S at (a-1,b), (a,b), (a-1,b+1), (a,b+1)
-        const Pt q = eval_pt(c, 1, I, J);
+    // ---- "+" adjoints, row s-9 ----
+    float4 pe0 = make_float4(0.f, 0.f, 0.f, 0.f), ps0 = pe0;
+    {
+      const int r = s - 9;
+      float4 de = pe0, ds = pe0;
+      if (ue_s != 0.f) {
+        // E(r,c): D reads S at (r-1,c), (r,c), (r-1,c+1), (r,c+1)
         float D[4];
-        const float4 n0 = V(c, G_SSI, I - 1, J), n1 = V(c, G_SSI, I, J);
-        const float4 n2 = V(c, G_SSI, I - 1, J + 1), n3 = V(c, G_SSI, I, J + 1);
-        const float4 own = V(c, G_ESI, I, J);
-  #pragma unroll
-        for (int d = 0; d < 4; ++d)
-          D[d] = fmaf(c.w, comp(n0, d) + comp(n1, d) + comp(n2, d) + comp(n3, d), comp(own, d));
-        point_adjoint<BMODE>(q, D, c.beta, uE, pE, dE);
+        smooth(R.SIE[r & 3][u], R.SIS[(r - 1) & 3][u], R.SIS[r & 3][u],
+               R.SIS[(r - 1) & 3][u + 1], R.SIS[r & 3][u + 1], w, D);
+        const Sten q = sten_e(R.A[r & 15] + u, R.X[(r - 2) & 15][u], R.X[(r - 1) & 15][u],
+                              R.X[r & 15][u], R.X[(r + 1) & 15][u]);
+        point_adjoint<BMODE>(q, D, k.beta, ue_s, pe0, de);
       }
-      if (uS != 0.f) {
-        // S(a,b): D reads E at (a,b-1), (a,b), (a+1,b-1), (a+1,b)
-        const Pt q = eval_pt(c, 2, I, J);
+      if (us_s != 0.f) {
+        // S(r,c): D reads E at (r,c-1), (r,c), (r+1,c-1), (r+1,c)
         float D[4];
-        const float4 n0 = V(c, G_ESI, I, J - 1), n1 = V(c, G_ESI, I, J);
-        const float4 n2 = V(c, G_ESI, I + 1, J - 1), n3 = V(c, G_ESI, I + 1, J);
-        const float4 own = V(c, G_SSI, I, J);
-  #pragma unroll
-        for (int d = 0; d < 4; ++d)
-          D[d] = fmaf(c.w, comp(n0, d) + comp(n1, d) + comp(n2, d) + comp(n3, d), comp(own, d));
-        point_adjoint<BMODE>(q, D, c.beta, uS, pS, dS);
+        smooth(R.SIS[r & 3][u], R.SIE[r & 3][u - 1], R.SIE[r & 3][u],
+               R.SIE[(r + 1) & 3][u - 1], R.SIE[(r + 1) & 3][u], w, D);
+        const Sten q = sten_s(R.X[r & 15] + u, R.A[(r - 1) & 15][u], R.A[r & 15][u],
+                              R.A[(r + 1) & 15][u], R.A[(r + 2) & 15][u]);
+        point_adjoint<BMODE>(q, D, k.beta, us_s, ps0, ds);
+      }
+      R.DE[r & 3][u] = de;
+      R.DS[r & 3][u] = ds;
+    }
+    // ---- "+" coefficients, row r = s-11 ----
+    {
+      const int r = s - 11;
+      // E(r,c) is read by S(r,c), S(r,c+1), S(r-1,c), S(r-1,c+1)
+      float sb[4];
+      float4 eh = make_float4(0.f, 0.f, 0.f, 0.f);
+      {
+        smooth(R.DE[r & 3][u], R.DS[r & 3][u], R.DS[r & 3][u + 1], R.DS[(r - 1) & 3][u],
+               R.DS[(r - 1) & 3][u + 1], w, sb);
+        const float4 pb = pe2;
+        if ((pb.x != 0.f || pb.y != 0.f || pb.z != 0.f || pb.w != 0.f) ||
+            (sb[0] != 0.f || sb[1] != 0.f || sb[2] != 0.f || sb[3] != 0.f)) {
+          const Sten q = sten_e(R.A[r & 15] + u, R.X[(r - 2) & 15][u], R.X[(r - 1) & 15][u],
+                                R.X[r & 15][u], R.X[(r + 1) & 15][u]);
+          float cf[4][3];
+          node_coefs(q, pb, sb, k2, cf);
+          // along row r (samples): targets columns c-1, c, c+1, c+2
+          eh = make_float4(cf[1][2], cf[0][0] + cf[1][1], cf[0][1] + cf[1][0], cf[0][2]);
+          // along column c (x values): rows r-2 .. r+1
+          xacc[0] += cf[3][2];
+          xacc[1] += cf[2][0] + cf[3][1];
+          xacc[2] += cf[2][1] + cf[3][0];
+          xacc[3] += cf[2][2];
+        }
+      }
+      R.EH[r & 1][u] = eh;
+      // S(r,c) is read by E(r,c), E(r+1,c), E(r,c-1), E(r+1,c-1)
+      float4 sh = make_float4(0.f, 0.f, 0.f, 0.f);
+      {
+        smooth(R.DS[r & 3][u], R.DE[r & 3][u], R.DE[(r + 1) & 3][u], R.DE[r & 3][u - 1],
+               R.DE[(r + 1) & 3][u - 1], w, sb);
+        const float4 pb = ps2;
+        if ((pb.x != 0.f || pb.y != 0.f || pb.z != 0.f || pb.w != 0.f) ||
+            (sb[0] != 0.f || sb[1] != 0.f || sb[2] != 0.f || sb[3] != 0.f)) {
+          const Sten q = sten_s(R.X[r & 15] + u, R.A[(r - 1) & 15][u], R.A[r & 15][u],
+                                R.A[(r + 1) & 15][u], R.A[(r + 2) & 15][u]);
+          float cf[4][3];
+          node_coefs(q, pb, sb, k2, cf);
+          // along row r (x values): targets columns c-2, c-1, c, c+1
+          sh = make_float4(cf[1][2], cf[0][0] + cf[1][1], cf[0][1] + cf[1][0], cf[0][2]);
+          // along column c (samples): rows r-1 .. r+2
+          aacc[0] += cf[3][2];
+          aacc[1] += cf[2][0] + cf[3][1];
+          aacc[2] += cf[2][1] + cf[3][0];
+          aacc[3] += cf[2][2];
+        }
+      }
+      R.SH[r & 3][u] = sh;
+
+      // ---- X_bar of row r-2 and the partial A_bar of row r-1 are complete ----
+      const int q = r - 2, p = r - 1;
+      const float4* shq = R.SH[q & 3] + u;
+      const float4* ehp = R.EH[p & 1] + u;
+      const float xb = xacc[0] + (shq[2].x + shq[1].y) + (shq[0].z + shq[-1].w) + gx_s;
+      const float ab = aacc[0] + (ehp[1].x + ehp[0].y) + (ehp[-1].z + ehp[-2].w) + ga_s;
+      if (col_out && q >= a0 && q < a1) ws.xb[ws.idx(q, c)] = xb;
+      if (col_out && p >= a0 && p < a1) ws.ab[ws.idx(p, c)] = ab;
+      xacc[0] = xacc[1]; xacc[1] = xacc[2]; xacc[2] = xacc[3]; xacc[3] = 0.f;
+      aacc[0] = aacc[1]; aacc[1] = aacc[2]; aacc[2] = aacc[3]; aacc[3] = 0.f;
+    }
+    pe2 = pe1; pe1 = pe0;
+    ps2 = ps1; ps1 = ps0;
+  }
+}
+
+// ---- k_bwd_cross ---------------------------------------------------------------
+// Lags: input row 0, x indicators 3, x adjoints 5, x coefficients 7; A_bar
+// of row s - 9 is complete at step s and written (column-folded) at s + 1.
+template <int BMODE>
+__global__ void __launch_bounds__(NT2, 3) k_bwd_cross(BwdArgs a, MethodConsts k, int rows) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  RingsCross<NT2>& R = *reinterpret_cast<RingsCross<NT2>*>(smem);
+  const int t = threadIdx.x;
+  const int64_t plane = blockIdx.z;
+  const int n = (int)a.n, m = (int)a.m;
+  const int nby = (int)gridDim.y;
+  const int b0 = (int)blockIdx.x * TW2;
+  const int b1 = min(b0 + TW2, m);
+  const int c = b0 - HL2 + t;
+  // A_bar rows of this band: image rows [r0, r1) plus the ghost rows that
+  // fold onto row 0 (first band) and row n-1 (last band)
+  const int r0 = (int)blockIdx.y * rows, r1 = min(r0 + rows, n);
+  const int a0 = blockIdx.y == 0 ? -GA : r0;
+  const int a1 = (int)blockIdx.y == nby - 1 ? n + GA : r1;
+  const float* xin = a.x + plane * a.x_sc + (int64_t)clampi(c, 0, m - 1) * a.x_sw;
+  const WsPlane ws = ws_plane(a, plane);
+  const bool cg = c >= -BWD_GHOST && c < m + BWD_GHOST;  // column on the workspace grid
+  // the thread writes grad_in column c; columns 0 and m-1 also sum the ghost
+  // columns folded onto them
+  const bool emit_col = c >= b0 && c < b1;
+  const bool fold_left = c == 0, fold_right = c == m - 1;
+  const float w = k.w;
+  const float k1 = k.kappa1 * k.kappa1;
+
+  {
+    float* z = reinterpret_cast<float*>(smem);
+    for (int i = t; i < (int)(sizeof(RingsCross<NT2>) / sizeof(float)); i += NT2) z[i] = 0.f;
+  }
+  const int u = t + PAD;
+  const int s_begin = a0 - 5, s_end = a1 - 1 + 10;
+  float pf = __ldg(xin + (int64_t)clampi(s_begin, 0, n - 1) * a.x_sh);
+  float pf2 = __ldg(xin + (int64_t)clampi(s_begin + 1, 0, n - 1) * a.x_sh);
+  // workspace values of the next step's rows, loaded one step ahead
+  auto ws_at = [&](const float* base, int r) -> float {
+    return (cg && r >= -BWD_GHOST && r < n + BWD_GHOST) ? base[ws.idx(r, c)] : 0.f;
+  };
+  float xbn = ws_at(ws.xb, s_begin - 5), abn = ws_at(ws.ab, s_begin - 9);
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};  // A_bar rows s-9 .. s-6 of this column
+  float rowsum = 0.f;                    // ghost rows folded onto an edge row
+  int emitted = -1;                      // grad_in row published in the previous step
+
+  for (int s = s_begin; s <= s_end; ++s) {
+    const float cur = pf;
+    pf = pf2;
+    pf2 = __ldg(xin + (int64_t)clampi(s + 2, 0, n - 1) * a.x_sh);
+    const float xb_s = xbn, ab_s = abn;
+    xbn = ws_at(ws.xb, s - 4);
+    abn = ws_at(ws.ab, s - 8);
+    __syncthreads();
+    R.A[s & 15][u] = cur;
+
+    // ---- grad_in row published in the previous step: fold the ghost columns ----
+    if (emitted >= 0 && emit_col) {
+      const float* af = R.AF[(s - 1) & 1] + u;
+      float v = af[0];
+      if (fold_left) v += (af[-5] + af[-4]) + (af[-3] + af[-2]) + af[-1];
+      if (fold_right) v += (af[1] + af[2]) + (af[3] + af[4]) + af[5];
+      a.gin[plane * a.gi_sc + (int64_t)emitted * a.gi_sh + (int64_t)c * a.gi_sw] = v;
+    }
+
+    // ---- x indicators, row s-3 ----
+    {
+      const int ra = s - 3;
+      const Sten q = sten_x(R.A[(ra - 1) & 15] + u, R.A[ra & 15] + u, R.A[(ra + 1) & 15] + u,
+                            R.A[(ra + 2) & 15] + u);
+      R.SIX[ra & 3][u] = indicators(q, k.kappa1, k.eps1);
+    }
+    // ---- x adjoints, row s-5 ----
+    {
+      const int ra = s - 5;
+      const float xb = xb_s;
+      float4 px = make_float4(0.f, 0.f, 0.f, 0.f), dx = px;
+      if (xb != 0.f) {
+        float D[4];
+        smooth(R.SIX[ra & 3][u], R.SIX[(ra - 1) & 3][u], R.SIX[(ra + 1) & 3][u],
+               R.SIX[ra & 3][u - 1], R.SIX[ra & 3][u + 1], w, D);
+        const Sten q = sten_x(R.A[(ra - 1) & 15] + u, R.A[ra & 15] + u,
+                              R.A[(ra + 1) & 15] + u, R.A[(ra + 2) & 15] + u);
+        point_adjoint<BMODE>(q, D, k.beta, xb, px, dx);
+      }
+      R.PX[ra & 3][u] = px;
+      R.DX[ra & 3][u] = dx;
+    }
+    // ---- x coefficients, row s-7 ----
+    {
+      const int ra = s - 7;
+      float sb[4];
+      smooth(R.DX[ra & 3][u], R.DX[(ra - 1) & 3][u], R.DX[(ra + 1) & 3][u],
+             R.DX[ra & 3][u - 1], R.DX[ra & 3][u + 1], w, sb);
+      const float4 pb = R.PX[ra & 3][u];
+      float2 c1 = make_float2(0.f, 0.f), c2 = c1, cm = c1;
+      if ((pb.x != 0.f || pb.y != 0.f || pb.z != 0.f || pb.w != 0.f) ||
+          (sb[0] != 0.f || sb[1] != 0.f || sb[2] != 0.f || sb[3] != 0.f)) {
+        const Sten q = sten_x(R.A[(ra - 1) & 15] + u, R.A[ra & 15] + u,
+                              R.A[(ra + 1) & 15] + u, R.A[(ra + 2) & 15] + u);
+        float cf[4][3];
+        node_coefs(q, pb, sb, k1, cf);
+        // targets (row offset, column offset): (0,0) d0.N0 + d1.N1,
+        // (1,1) d0.N1 + d1.N0, (2,2) d0.N2, (-1,-1) d1.N2, (0,1) d2.N0 + d3.N1,
+        // (1,0) d2.N1 + d3.N0, (2,-1) d2.N2, (-1,2) d3.N2
+        acc[2] += cf[0][0] + cf[1][1];  // row ra   (= s-7)
+        acc[3] += cf[2][1] + cf[3][0];  // row ra+1
+        c1 = make_float2(cf[2][0] + cf[3][1], cf[0][1] + cf[1][0]);
+        c2 = make_float2(cf[0][2], cf[3][2]);
+        cm = make_float2(cf[1][2], cf[2][2]);
+      }
+      R.C1[ra & 1][u] = c1;
+      R.C2[ra & 1][u] = c2;
+      R.CM[ra & 1][u] = cm;
+    }
+    // ---- contributions of x row s-8 from the neighbouring columns ----
+    {
+      const int rp = s - 8;
+      const float2 c1 = R.C1[rp & 1][u - 1];  // from column c-1: rows rp, rp+1
+      const float2 c2 = R.C2[rp & 1][u - 2];  // from column c-2: rows rp+2, rp-1
+      const float2 cm = R.CM[rp & 1][u + 1];  // from column c+1: rows rp-1, rp+2
+      acc[0] += c2.y + cm.x;
+      acc[1] += c1.x;
+      acc[2] += c1.y;
+      acc[3] += c2.x + cm.y;
+    }
+    // ---- A_bar of row s-9 is complete ----
+    {
+      const int q = s - 9;
+      const float ab = acc[0] + ab_s;
+      acc[0] = acc[1]; acc[1] = acc[2]; acc[2] = acc[3]; acc[3] = 0.f;
+      emitted = -1;
+      if (q >= a0 && q < a1) {
+        rowsum += ab;
+        // rows -GA..0 fold onto row 0, rows n-1..n+GA-1 onto row n-1
+        if (q >= 0 && (q < n - 1 || q == n - 1 + GA)) {
+          emitted = min(q, n - 1);
+          R.AF[s & 1][u] = rowsum;
+          rowsum = 0.f;
+        }
       }
     }
-    V(c, G_EP, I, J) = f4(pE);
-    V(c, G_ED, I, J) = f4(dE);
-    V(c, G_SP, I, J) = f4(pS);
-    V(c, G_SD, I, J) = f4(dS);
   }
 }
 
-// SI_bar of the four directions at a point: its own D_bar plus w times the
-// D_bar of the points whose D reads it (gX, gE, gS: the D_bar groups).
-__device__ __forceinline__ void si_bar4(const Ctx& c, int type, int a, int b, int gX, int gE,
-                                        int gS, float sb[4]) {
-  float4 own, n0, n1, n2, n3;
-  if (type == 0) {
-    own = V0(c, gX, a, b);
-    n0 = V0(c, gX, a - 1, b); n1 = V0(c, gX, a + 1, b);
-    n2 = V0(c, gX, a, b - 1); n3 = V0(c, gX, a, b + 1);
-  } else if (type == 1) {  // E(a,b) is read by S(a,b), S(a,b+1), S(a-1,b), S(a-1,b+1)
-    own = V0(c, gE, a, b);
-    n0 = V0(c, gS, a, b); n1 = V0(c, gS, a, b + 1);
-    n2 = V0(c, gS, a - 1, b); n3 = V0(c, gS, a - 1, b + 1);
-  } else {  // S(a,b) is read by E(a,b), E(a+1,b), E(a,b-1), E(a+1,b-1)
-    own = V0(c, gS, a, b);
-    n0 = V0(c, gE, a, b); n1 = V0(c, gE, a + 1, b);
-    n2 = V0(c, gE, a, b - 1); n3 = V0(c, gE, a + 1, b - 1);
-  }
-#pragma unroll
-  for (int d = 0; d < 4; ++d)
-    sb[d] = comp(own, d) + c.w * (comp(n0, d) + comp(n1, d) + comp(n2, d) + comp(n3, d));
-}
-
-// Node coefficients of every stencil of `type` at (I, J), stored at scalar
-// slot co + k*3 + t (gP: the p_bar group; gX, gE, gS: the D_bar groups).
-__device__ __forceinline__ void coef_point(const Ctx& c, int type, int I, int J, int gP, int gX,
-                                           int gE, int gS, int co) {
-  const float kap = type == 0 ? c.kap1 : c.kap2;
-  const float k2 = kap * kap;
-  const float4 pb4 = V(c, gP, I, J);
-  float sb[4];
-  si_bar4(c, type, I, J, gX, gE, gS, sb);
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const float pbar = comp(pb4, k);
-    const float sbar = sb[k];
-    float c0 = 0.f, c1 = 0.f, c2 = 0.f;
-    if (pbar != 0.f || sbar != 0.f) {
-      const float n0 = node(c, type, k, 0, I, J);
-      const float n1 = node(c, type, k, 1, I, J);
-      const float n2 = node(c, type, k, 2, I, J);
-      const float g = n1 - n0;
-      const float s = fmaf(-2.f, n1, n0 + n2);
-      c0 = fmaf(0.375f, pbar, (2.f * k2 * s - 2.f * g) * sbar);
-      c1 = fmaf(0.75f, pbar, (2.f * g - 4.f * k2 * s) * sbar);
-      c2 = fmaf(-0.125f, pbar, 2.f * k2 * s * sbar);
-    }
-    W(c, co + 3 * k + 0, I, J) = c0;
-    W(c, co + 3 * k + 1, I, J) = c1;
-    W(c, co + 3 * k + 2, I, J) = c2;
-  }
-}
-
-__global__ void k_coef2(BwdArgs a, MethodConsts k) {
-  Ctx c; int I0, J;
-  if (!setup<R_COEF2>(a, k, c, I0, J)) return;
-  for (int r = 0; r < R_COEF2; ++r) {
-    const int I = I0 + r * BWD_BY;
-    if (I >= c.n + G) break;
-    // E points whose adjoint can be nonzero: rows 0..n, columns -1..m-1;
-    // S points: rows -1..n-1, columns 0..m.  Elsewhere the coefficients are 0.
-    const bool e_live = I >= 0 && I <= c.n && J >= -1 && J < c.m;
-    const bool s_live = I >= -1 && I < c.n && J >= 0 && J <= c.m;
-    if (e_live) {
-      coef_point(c, 1, I, J, G_EP, 0, G_ED, G_SD, S_ECO);
-    } else {
-  #pragma unroll
-      for (int q = 0; q < 12; ++q) W(c, S_ECO + q, I, J) = 0.f;
-    }
-    if (s_live) {
-      coef_point(c, 2, I, J, G_SP, 0, G_ED, G_SD, S_SCO);
-    } else {
-  #pragma unroll
-      for (int q = 0; q < 12; ++q) W(c, S_SCO + q, I, J) = 0.f;
+// Rows per band: the band count that minimises waves x (rows + fill steps).
+int band_rows(int64_t rows_total, int64_t ctas_per_band_row, int fill, int resident) {
+  int best = (int)rows_total;
+  double best_cost = 1e300;
+  for (int bands = 1; bands <= 64; ++bands) {
+    const int64_t h = (rows_total + bands - 1) / bands;
+    if (h < 16 && bands > 1) break;
+    const int64_t ctas = ctas_per_band_row * bands;
+    const int64_t waves = (ctas + resident - 1) / resident;
+    const double cost = double(waves) * double(h + fill);
+    if (cost < best_cost - 1e-9) {
+      best_cost = cost;
+      best = (int)h;
     }
   }
-}
-
-// Sum over the stencils of `type` whose node on `lattice` sits at (i, j).
-__device__ __forceinline__ float gather(const Ctx& c, int type, int lattice, int i, int j,
-                                        int co) {
-  float acc = 0.f;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    if (lattice_of(type, k) != lattice) continue;
-#pragma unroll
-    for (int t = 0; t < 3; ++t)
-      acc += W0(c, co + 3 * k + t, i - off_of(type, k, t, 0), j - off_of(type, k, t, 1));
-  }
-  return acc;
-}
-
-// X_bar (plus the x-point output gradient) and A_bar from phase 2, then at
-// once the x point's own adjoint from that X_bar (phase 1): p_bar, D_bar of
-// the x points, into the groups the "+" points used (no thread of this
-// kernel reads them).
-template <int BMODE>
-__global__ void k_gather2_xadj(BwdArgs a, MethodConsts k) {
-  Ctx c; int I0, J;
-  if (!setup<R_G2>(a, k, c, I0, J)) return;
-  for (int r = 0; r < R_G2; ++r) {
-    const int I = I0 + r * BWD_BY;
-    if (I >= c.n + G) break;
-    const int64_t plane = blockIdx.z;
-    float xb = gather(c, 1, 1, I, J, S_ECO) + gather(c, 2, 1, I, J, S_SCO);
-    float ab = gather(c, 1, 0, I, J, S_ECO) + gather(c, 2, 0, I, J, S_SCO);
-    if (I >= 0 && I < c.n && J >= 0 && J < c.m) {
-      xb += gout_at(a, plane, 2 * (int64_t)I + 1, 2 * (int64_t)J + 1);
-      ab += gout_at(a, plane, 2 * (int64_t)I, 2 * (int64_t)J);
-    }
-    W(c, S_AB, I, J) = ab;
-    // ---- phase-1 adjoint of this x point ----
-    float pX[4] = {0.f, 0.f, 0.f, 0.f}, dX[4] = {0.f, 0.f, 0.f, 0.f};
-    if (xb != 0.f && I >= -4 && I < c.n + 4 && J >= -4 && J < c.m + 4) {
-      const Pt q = eval_pt(c, 0, I, J);
-      float D[4];
-      d_x<BMODE>(c, I, J, q.si, D);
-      point_adjoint<BMODE>(q, D, c.beta, xb, pX, dX);
-    }
-    V(c, G_EP, I, J) = f4(pX);
-    V(c, G_ED, I, J) = f4(dX);
-  }
-}
-
-__global__ void k_coef1(BwdArgs a, MethodConsts k) {
-  Ctx c; int I0, J;
-  if (!setup<R_COEF1>(a, k, c, I0, J)) return;
-  for (int r = 0; r < R_COEF1; ++r) {
-    const int I = I0 + r * BWD_BY;
-    if (I >= c.n + G) break;
-    if (I >= -5 && I < c.n + 5 && J >= -5 && J < c.m + 5) {
-      coef_point(c, 0, I, J, G_EP, G_ED, 0, 0, S_ECO);
-    } else {
-  #pragma unroll
-      for (int q = 0; q < 12; ++q) W(c, S_ECO + q, I, J) = 0.f;
-    }
-  }
-}
-
-__global__ void k_gather1(BwdArgs a, MethodConsts k) {
-  Ctx c; int I0, J;
-  if (!setup<R_G1>(a, k, c, I0, J)) return;
-  for (int r = 0; r < R_G1; ++r) {
-    const int I = I0 + r * BWD_BY;
-    if (I >= c.n + G) break;
-    W(c, S_AB, I, J) += gather(c, 0, 0, I, J, S_ECO);
-  }
-}
-
-// grad_in(i, j) = sum of A_bar over the extended cells that clamp to (i, j).
-__global__ void k_fold(BwdArgs a, MethodConsts k) {
-  Ctx c; int I0, J;
-  if (!setup<R_FOLD>(a, k, c, I0, J)) return;
-  for (int r = 0; r < R_FOLD; ++r) {
-    const int I = I0 + r * BWD_BY;
-    if (I >= c.n + G) break;
-    if (I < 0 || I >= c.n || J < 0 || J >= c.m) continue;
-    const int i0 = I == 0 ? -G : I, i1 = I == c.n - 1 ? c.n - 1 + G : I;
-    const int j0 = J == 0 ? -G : J, j1 = J == c.m - 1 ? c.m - 1 + G : J;
-    float acc = 0.f;
-    for (int ii = i0; ii <= i1; ++ii)
-      for (int jj = j0; jj <= j1; ++jj) acc += W(c, S_AB, ii, jj);
-    const int64_t plane = blockIdx.z;
-    a.gin[plane * a.gi_sc + (int64_t)I * a.gi_sh + (int64_t)J * a.gi_sw] = acc;
-  }
+  return best;
 }
 
 template <int BMODE>
 cudaError_t launch_all(const BwdArgs& a, const MethodConsts& k, cudaStream_t st) {
-  const dim3 block(32, BWD_BY);
-  auto grid = [&](int R) {
-    return dim3((unsigned)((a.m + 2 * G + 31) / 32),
-                (unsigned)((a.n + 2 * G + BWD_BY * R - 1) / (BWD_BY * R)), (unsigned)a.planes);
-  };
-  k_xsi<<<grid(R_XSI), block, 0, st>>>(a, k);
-  k_xval<BMODE><<<grid(R_XVAL), block, 0, st>>>(a, k);
-  k_psi<<<grid(R_PSI), block, 0, st>>>(a, k);
-  k_padj<BMODE><<<grid(R_PADJ), block, 0, st>>>(a, k);
-  k_coef2<<<grid(R_COEF2), block, 0, st>>>(a, k);
-  k_gather2_xadj<BMODE><<<grid(R_G2), block, 0, st>>>(a, k);
-  k_coef1<<<grid(R_COEF1), block, 0, st>>>(a, k);
-  k_gather1<<<grid(R_G1), block, 0, st>>>(a, k);
-  k_fold<<<grid(R_FOLD), block, 0, st>>>(a, k);
+  const size_t sm1 = sizeof(RingsPlus<NT1>), sm2 = sizeof(RingsCross<NT2>);
+  cudaError_t e = cudaFuncSetAttribute(k_bwd_plus<BMODE>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_bwd_cross<BMODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sm2);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, occ1 = 0, occ2 = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+    return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, k_bwd_plus<BMODE>, NT1, sm1)) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, k_bwd_cross<BMODE>, NT2, sm2)) !=
+      cudaSuccess)
+    return e;
+  if (occ1 < 1 || occ2 < 1) return cudaErrorInvalidConfiguration;
+  // k_bwd_plus: the extended grid, rows and columns [-2, n+2) x [-2, m+2)
+  const int64_t ext_n = a.n + 2 * BWD_GHOST, ext_m = a.m + 2 * BWD_GHOST;
+  const int64_t sx1 = (ext_m + TW1 - 1) / TW1;
+  const int h1 = band_rows(ext_n, sx1 * a.planes, 19, occ1 * sms);
+  const dim3 g1((unsigned)sx1, (unsigned)((ext_n + h1 - 1) / h1), (unsigned)a.planes);
+  k_bwd_plus<BMODE><<<g1, NT1, sm1, st>>>(a, k, h1);
+  // k_bwd_cross: image rows and columns, ghosts folded at the edges
+  const int64_t sx2 = (a.m + TW2 - 1) / TW2;
+  const int h2 = band_rows(a.n, sx2 * a.planes, 15, occ2 * sms);
+  const dim3 g2((unsigned)sx2, (unsigned)((a.n + h2 - 1) / h2), (unsigned)a.planes);
+  k_bwd_cross<BMODE><<<g2, NT2, sm2, st>>>(a, k, h2);
   return cudaGetLastError();
 }
 
 }  // namespace
 
 size_t bwd_workspace_bytes(int64_t n, int64_t m, int64_t planes) {
-  // per plane: the extended cell count padded to a multiple of 4 (float4 planes)
-  const size_t cells = ((size_t)(n + 2 * G) * (size_t)(m + 2 * G) + 3) & ~(size_t)3;
-  return sizeof(float) * (size_t)BWD_ARRAYS * cells * (size_t)planes;
+  // X_bar and the partial A_bar on the grid extended by BWD_GHOST cells
+  return sizeof(float) * 2 * (size_t)(n + 2 * BWD_GHOST) * (size_t)(m + 2 * BWD_GHOST) *
+         (size_t)planes;
 }
 
 cudaError_t launch_zoom2x_bwd(const BwdArgs& a, const MethodConsts& k, int bmode,

@@ -9,8 +9,7 @@
 
 namespace wdweno {
 
-constexpr int BWD_GHOST = 7;    // extension cells per side of the work grid
-constexpr int BWD_ARRAYS = 55;  // FP32 arrays per plane in the workspace
+constexpr int BWD_GHOST = 2;  // extension cells per side of the workspace grid
 
 struct BwdArgs {
   const float* x;
@@ -21,7 +20,7 @@ struct BwdArgs {
   int64_t g_sc, g_sh, g_sw;
   int64_t gi_sc, gi_sh, gi_sw;
   int64_t orows, ocols;
-  float* ws;  // BWD_ARRAYS * (n + 2G) * (m + 2G) * planes floats
+  float* ws;  // 2 * (n + 2 BWD_GHOST) * (m + 2 BWD_GHOST) * planes floats
 };
 
 size_t bwd_workspace_bytes(int64_t n, int64_t m, int64_t planes);

@@ -109,7 +109,7 @@ def test_bwd_rejects_bad_arguments_without_launching():
     go = _img(FAKE_OUT, 8, 10, 1)
     gi = _img(0x30000000, 4, 5, 1)
     need = B.weno_zoom2x_bwd_workspace_bytes(x)
-    assert need == 4 * 55 * (((4 + 14) * (5 + 14) + 3) // 4 * 4)  # cells padded to a multiple of 4
+    assert need == 4 * 2 * (4 + 4) * (5 + 4)  # X_bar and partial A_bar, 2 ghost cells a side
     assert B.weno_zoom2x_bwd(x, go, gi, p, None, need, None) == B.WENO_EWORKSPACE
     assert B.weno_zoom2x_bwd(x, go, gi, p, 0x40000000, need - 1, None) == B.WENO_EWORKSPACE
     assert B.weno_zoom2x_bwd(x, go, gi, p, 0x40000004, need, None) == B.WENO_EWORKSPACE
@@ -118,6 +118,7 @@ def test_bwd_rejects_bad_arguments_without_launching():
     assert B.weno_zoom2x_bwd(x, go, _img(FAKE_IN, 4, 5, 1), p, 0x40000000, need,
                              None) == B.WENO_EINVAL  # grad_in aliases x
     assert B.weno_zoom2x_bwd_workspace_bytes(_img(FAKE_IN, 0, 5, 1)) == 0
+
 
 
 def test_batched_rejects_bad_arguments_without_launching():
