@@ -55,9 +55,11 @@ ALGO_MUFU_PER_PXCH = 15
 ALGO_BYTES_PER_PXCH = {"u8": 5, "f16": 10, "bf16": 10, "f32": 20}
 FP32_LANES_PER_SM = 128
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "zoom2x_fwd_4k_u8.md")
-# The forward kernel's code: its tile body, device helpers and kernel
-# template (the .cu files around them only choose which instantiation runs).
+# The forward kernel's code: its tile bodies (one and two columns per
+# thread), device helpers and kernel templates (the .cu files around them
+# only choose which instantiation runs).
 KERNEL_SOURCES = ["paper_2312_00229_gb300/csrc/wd_fwd_tile.cuh",
+                  "paper_2312_00229_gb300/csrc/wd_fwd_tile2.cuh",
                   "paper_2312_00229_gb300/csrc/wd_common.cuh",
                   "paper_2312_00229_gb300/csrc/wd_fwd_kernels.cuh"]
 
@@ -437,7 +439,9 @@ def run_ours(args):
     roofline = {"bound": "alu", "achieved": round(achieved_ops / 1e12, 3),
                 "peak": round(alu_peak / 1e12, 3), "unit": "Top/s",
                 "frac": round(achieved_ops / alu_peak, 4), "traffic": traffic,
-                "kernel": "zoom2x_fwd_kernel<B2R, u8->u8>",
+                "kernel": ("zoom2x_fwd_kernel2<B2R, u8->u8> (two columns per thread)"
+                           if tw in (246, 118) else "zoom2x_fwd_kernel<B2R, u8->u8>"),
+                "tile": f"{rpb or 'default'} rows x {tw or 'default'} columns",
                 "ops_per_pxch": ALGO_FP32_OPS_PER_PXCH,
                 "peak_kind": "nominal FP32-pipe peak (not measured): SMs x 128 lanes x "
                              "maximum SM clock",
@@ -461,7 +465,7 @@ def run_ours(args):
                        "beta": 2.0, "global_batch": FRAMES_PER_STEP,
                        "step": f"{FRAMES_PER_STEP} frames, one forward launch each",
                        "rows_per_band": rpb or "library default",
-                       "strip_width": tw or "library default (247 at this width)",
+                       "strip_width": tw or "library default (246 at this width)",
                        "autotune_ms": {f"{r}x{w}": round(v, 4) for (r, w), v in tune_ms.items()},
                        "l2": f"{R} rotating input/output buffer sets "
                              f"({R * 5 * H * W * C / 1e9:.2f} GB) > 129 MB L2",
@@ -719,11 +723,18 @@ def run_case(args):
                 for _ in range(ROTATING_SETS)]
         it = [0]
 
+        # the tile shape the autotuner cached for this size class (the
+        # headline run tunes it), else the library default
+        from paper_2312_00229_gb300 import autotune
+        shape = (autotune.lookup(xs[0], torch.uint8, "chw"),
+                 autotune.lookup_width(xs[0], torch.uint8, "chw"))
+
         def step():
             i = it[0] % ROTATING_SETS
             it[0] += 1
-            api.zoom2x_fwd(xs[i], out=outs[i], rows_per_tile=0)
-        work = f"{W}x{H}x{C} uint8 -> {2 * W}x{2 * H}, {ROTATING_SETS} rotating buffer sets"
+            api.zoom2x_fwd(xs[i], out=outs[i], rows_per_tile=shape[0], tile_width=shape[1])
+        work = (f"{W}x{H}x{C} uint8 -> {2 * W}x{2 * H}, {ROTATING_SETS} rotating buffer sets, "
+                f"tile shape {shape[0] or 'default'} rows x {shape[1] or 'default'} columns")
     elif args.case == "resample3x":
         hd = torch.from_numpy(scenes.planar(scenes.piecewise_smooth(
             1080, 1920, seed=scenes.seed_for(2)))).to(dev)

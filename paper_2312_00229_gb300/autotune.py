@@ -1,10 +1,13 @@
 """Autotuner for the tile shape of the forward and batched zoom.
 
 The CUDA kernels take the band height (coarse rows per CTA) as a run-time
-parameter, and the strip width (output columns per CTA, one thread per
-coarse column) as one of two built widths: 247 (256 threads) or 119 (128
-threads).  The one-launch forward picks the width from the image width; the
-batched launch takes it from the caller.  This module times candidate shapes
+parameter, and the strip width (output columns per CTA) as one of the built
+tile shapes, which also fix the coarse columns per thread (the threads that
+share one quad column's work): 247 (256 threads, one column each), 119 (128
+threads, one column), 246 (128 threads, two columns each) or 118 (64
+threads, two columns).  The one-launch forward picks a shape from the image
+width; the batched launch takes one of the one-column widths from the
+caller.  This module times candidate shapes
 on the current GPU with CUDA events and caches the fastest per size class in
 a JSON file, keyed by device name, storage types, layout and size class
 (planes and the image sides rounded up to powers of two).
@@ -25,7 +28,10 @@ CACHE_PATH = os.environ.get(
     "WDWENO_AUTOTUNE_CACHE",
     os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json"))
 CANDIDATES = (0, 16, 24, 32, 48, 64, 96, 128, 192)
-TILE_WIDTHS = (247, 119)  # output columns per CTA: 256 and 128 threads
+# output columns per CTA: one column per thread (256 and 128 threads) and
+# two columns per thread (128 and 64 threads)
+TILE_WIDTHS = (247, 119, 246, 118)
+BATCHED_TILE_WIDTHS = (247, 119)  # the persistent kernel runs the one-column tile
 
 _lock = threading.Lock()
 _cache: Optional[Dict[str, int]] = None
@@ -131,7 +137,7 @@ def _batched_key(images: Sequence[torch.Tensor], out_dtype, layout: str) -> str:
 
 def tune_batched(images: Sequence[torch.Tensor], params=None, out_dtype=None,
                  layout: str = "chw", candidates: Iterable[int] = (16, 32, 64, 128),
-                 widths: Iterable[int] = TILE_WIDTHS,
+                 widths: Iterable[int] = BATCHED_TILE_WIDTHS,
                  reps: int = 5) -> Dict[Tuple[int, int], float]:
     """Times the persistent batched launch for each (band height, tile width)
     and caches the fastest under the batch's size class (dtype, layout, image

@@ -37,22 +37,31 @@ int sm_count() {
   return cached[dev];
 }
 
-// CTA width for a requested tile width (output columns per CTA): 247 -> 256
-// threads, 119 -> 128; 0 for any other width.
-int threads_for_width(int tile_width) {
-  if (tile_width == tile_width_fwd()) return threads_fwd();
-  if (tile_width == tile_width_fwd() - (threads_fwd() - 128)) return 128;
-  return 0;
+// CTA shape for a requested tile width (output columns per CTA): 247 -> 256
+// threads of one column, 119 -> 128 threads of one column, 246 -> 128
+// threads of two columns, 118 -> 64 threads of two columns; false for any
+// other width.
+bool shape_for_width(int tile_width, int* threads, int* cols) {
+  *cols = 1;
+  if (tile_width == tile_width_fwd()) { *threads = threads_fwd(); return true; }
+  if (tile_width == tile_width_fwd() - (threads_fwd() - 128)) { *threads = 128; return true; }
+  *cols = 2;
+  if (tile_width == 2 * 128 - 10) { *threads = 128; return true; }
+  if (tile_width == 2 * 64 - 10) { *threads = 64; return true; }
+  return false;
 }
 
 // Band height for a one-launch forward: choose the number of bands B that
 // minimises (waves of CTAs) x (rows per band + pipeline fill), i.e. balance
-// the tail of the last wave against the fixed per-band cost.
-int64_t default_rows_per_band(int64_t n, int64_t m, int64_t planes, int threads) {
+// the tail of the last wave against the fixed per-band cost.  `cols` coarse
+// columns per thread: one-column CTAs of 256 (128) threads keep 2 (4)
+// resident per SM, two-column CTAs of 128 (64) threads 3 (6).
+int64_t default_rows_per_band(int64_t n, int64_t m, int64_t planes, int threads, int cols = 1) {
   const int sms = sm_count();
   if (sms <= 0) return kDefaultRowsPerBand;
-  const int64_t slots = (int64_t)sms * kFwdCtasPerSm * (threads_fwd() / threads);
-  const int64_t tw = threads - 9;
+  const int64_t per_sm = cols == 2 ? 3 * 128 / threads : kFwdCtasPerSm * (threads_fwd() / threads);
+  const int64_t slots = (int64_t)sms * per_sm;
+  const int64_t tw = cols == 2 ? 2 * threads - 10 : threads - 9;
   const int64_t strips = (m + tw - 1) / tw;
   const int64_t base = strips * planes;
   const int64_t fill = 7;  // extra steps per band: 4 + 5 halo rows + 2 pipeline steps
@@ -225,6 +234,9 @@ FwdArgs make_fwd_args(const weno_image* in, int in_t, const weno_image* out, int
   const uintptr_t base = reinterpret_cast<uintptr_t>(out->data);
   a.out_vec = (out->stride_w == 1) && (out->stride_h % 2 == 0) && (out->stride_c % 2 == 0) &&
               (base % uintptr_t(2 * esz) == 0);
+  a.out_vec4 = (out->stride_w == 1) && (out->stride_h % 4 == 0) && (out->stride_c % 4 == 0) &&
+               (base % uintptr_t(4 * esz) == 0);
+  a.cols = 1;
   return a;
 }
 
@@ -309,17 +321,22 @@ int weno_zoom2x_fwd_tiled(const weno_image* in, weno_dtype in_t, const weno_imag
   int rc = check_pair(in, in_t, out, out_t, p, &orows, &ocols);
   if (rc != WENO_OK) return rc;
   if (rows_per_tile < 0 || rows_per_tile > 4096) return WENO_EINVAL;
-  const int threads = tile_width == 0 ? fwd_threads_for(in->width) : threads_for_width(tile_width);
-  if (threads == 0) return WENO_EINVAL;
+  int threads = 0, cols = 1;
+  if (tile_width == 0) {
+    fwd_shape_for(in->width, &threads, &cols);
+  } else if (!shape_for_width(tile_width, &threads, &cols)) {
+    return WENO_EINVAL;
+  }
   MethodConsts k;
   int bmode;
   if (!fold_consts(p, &k, &bmode)) return WENO_EINVAL;
   const int64_t rpb = rows_per_tile > 0 ? rows_per_tile
                                         : default_rows_per_band(in->height, in->width,
-                                                                in->channels, threads);
+                                                                in->channels, threads, cols);
   if (bmode == B2 && direct_b2_ok(p, in_t)) bmode = B2R;
   FwdArgs a = make_fwd_args(in, in_t, out, out_t, orows, ocols, rpb);
   a.threads = threads;
+  a.cols = cols;
   if ((a.n + rpb - 1) / rpb > 65535) return WENO_ERANGE;
   cudaError_t e = launch_zoom2x_fwd(a, k, bmode, static_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? WENO_OK : WENO_ECUDA;
@@ -389,8 +406,9 @@ int weno_zoom2x_batched(int count, const weno_image* d_in, weno_dtype in_t,
   if (!workspace || workspace_bytes < batched_workspace_bytes(count)) return WENO_EWORKSPACE;
   if (reinterpret_cast<uintptr_t>(workspace) % 16 != 0) return WENO_EWORKSPACE;
   if (rows_per_tile < 0 || rows_per_tile > 4096) return WENO_EINVAL;
-  const int threads = tile_width == 0 ? threads_fwd() : threads_for_width(tile_width);
-  if (threads == 0) return WENO_EINVAL;
+  int threads = threads_fwd(), cols = 1;
+  if (tile_width != 0 && (!shape_for_width(tile_width, &threads, &cols) || cols != 1))
+    return WENO_EINVAL;  // the persistent kernel runs the one-column tile
   MethodConsts k;
   int bmode;
   if (!fold_consts(p, &k, &bmode)) return WENO_EINVAL;

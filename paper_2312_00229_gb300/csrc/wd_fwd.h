@@ -18,14 +18,16 @@ struct FwdArgs {
   int64_t orows, ocols;          // output extent (2n or 2n-1, ...)
   int64_t rows_per_band;
   int out_vec;                   // unit column stride and 2-element aligned rows
-  int threads;                   // CTA width: 256 or 128 (fwd_threads_for)
+  int out_vec4;                  // unit column stride and 4-element aligned rows
+  int threads;                   // CTA width: 256 or 128 (one column), 128 or 64 (two)
+  int cols;                      // coarse columns per thread: 1, or 2 (paired tile)
 };
 
-// CTA width of a one-launch forward over images m columns wide: 128 when
-// its strips (119 output columns) need no more threads across the width than
-// 256-thread strips (247 output columns), else 256 (measured: the narrow
-// form's finer grid wins when the thread counts tie).
-int fwd_threads_for(int64_t m);
+// CTA shape of a one-launch forward over images m columns wide: `threads`
+// per CTA and `cols` coarse columns per thread (1: 256 or 128 threads, 247
+// or 119 output columns per strip; 2: 128 or 64 threads, 246 or 118), the
+// one that spends the fewest weighted column-steps across the width.
+void fwd_shape_for(int64_t m, int* threads, int* cols);
 
 int tile_width_fwd();
 int threads_fwd();

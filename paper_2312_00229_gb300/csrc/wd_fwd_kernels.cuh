@@ -5,6 +5,7 @@
 
 #include "wd_batched.h"
 #include "wd_fwd_tile.cuh"
+#include "wd_fwd_tile2.cuh"
 
 #ifndef WDWENO_FWD_MIN_BLOCKS
 #define WDWENO_FWD_MIN_BLOCKS 2
@@ -30,8 +31,27 @@ __global__ void __launch_bounds__(NT, fwd_min_blocks<NT>())
   fwd_tile::zoom2x_fwd_tile<BMODE, IO, NT>(a, k, ex, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
+// Two coarse columns per thread (wd_fwd_tile2.cuh): 2 NT columns per CTA.
+template <int BMODE, class IO, int NT>
+__global__ void __launch_bounds__(NT, 3 * 128 / NT)
+    zoom2x_fwd_kernel2(FwdArgs a, MethodConsts k) {
+  __shared__ fwd_tile::Exchange2<NT> ex;
+  fwd_tile::zoom2x_fwd_tile2<BMODE, IO, NT>(a, k, ex, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
 template <int BMODE, class IO>
 cudaError_t launch_fwd(const FwdArgs& a, const MethodConsts& k, cudaStream_t stream) {
+  if (a.cols == 2) {
+    const int nt = a.threads == 64 ? 64 : 128;
+    const int64_t tw = 2 * nt - 10;
+    dim3 grid((unsigned)((a.m + tw - 1) / tw),
+              (unsigned)((a.n + a.rows_per_band - 1) / a.rows_per_band), (unsigned)a.planes);
+    if (nt == 64)
+      zoom2x_fwd_kernel2<BMODE, IO, 64><<<grid, nt, 0, stream>>>(a, k);
+    else
+      zoom2x_fwd_kernel2<BMODE, IO, 128><<<grid, nt, 0, stream>>>(a, k);
+    return cudaGetLastError();
+  }
   const int nt = a.threads == fwd_tile::THREADS_NARROW ? fwd_tile::THREADS_NARROW : THREADS;
   const int64_t tw = nt - 9;
   dim3 grid((unsigned)((a.m + tw - 1) / tw),

@@ -449,6 +449,10 @@ struct TypedIO {
                                                 int clampf) {
     store2_typed<TOut>(out, idx, v0, v1, clampf);
   }
+  __device__ __forceinline__ static void store4(void* out, int64_t idx, float v0, float v1,
+                                                float v2, float v3, int, int clampf) {
+    store4_typed<TOut>(out, idx, v0, v1, v2, v3, clampf);
+  }
 };
 
 // Storage types chosen at run time (any in/out pair).
@@ -466,6 +470,10 @@ struct DynIO {
   __device__ __forceinline__ static void store2(void* out, int64_t idx, float v0, float v1,
                                                 int dt, int clampf) {
     store2_vec(out, idx, v0, v1, dt, clampf);
+  }
+  __device__ __forceinline__ static void store4(void* out, int64_t idx, float v0, float v1,
+                                                float v2, float v3, int dt, int clampf) {
+    store4_vec(out, idx, v0, v1, v2, v3, dt, clampf);
   }
 };
 

@@ -337,11 +337,46 @@ def test_fwd_narrow_and_wide_ctas_agree_bitwise(dt, mode):
     parity.compare(a.cpu(), ref, dt)
 
 
+@pytest.mark.parametrize("dt", ["u8", "f16", "bf16", "f32"])
+@pytest.mark.parametrize("mode", [0, 1])
+def test_fwd_paired_columns_agree_bitwise(dt, mode):
+    """Two coarse columns per thread (tile widths 246 and 118: 128 and 64
+    threads) form every value by the same expressions as one column per
+    thread, so the outputs agree bit for bit; widths end the last strip
+    anywhere, odd widths leave one column of a pair idle, and 2n-1 mode
+    drops the last fine column of a quad."""
+    p = api.Params(out_mode=mode)
+    shapes = [(9, 1), (5, 2), (13, 117), (21, 118), (17, 119), (11, 245), (40, 246),
+              (23, 247), (37, 512), (6, 1001)]
+    for shape in shapes:
+        A = RNG.random((2,) + shape)
+        x = parity.encode(A, dt).to(DEV)
+        ref1 = api.zoom2x_fwd(x, p, tile_width=247)
+        for tw in (246, 118):
+            got = api.zoom2x_fwd(x, p, tile_width=tw)
+            torch.cuda.synchronize()
+            assert torch.equal(got, ref1), (dt, mode, shape, tw)
+
+
+def test_fwd_paired_columns_strided_views():
+    """Output rows not aligned to four elements (a column-cropped view) take
+    the per-element stores of the paired tile."""
+    A = RNG.random((3, 30, 77))
+    x = parity.encode(A, "u8").to(DEV)
+    big = torch.full((3, 60, 160), 7, dtype=torch.uint8, device=DEV)
+    view = big[:, :, 1:155]
+    api.zoom2x_fwd(x, out=view, tile_width=246)
+    ref = api.zoom2x_fwd(x, tile_width=247)
+    torch.cuda.synchronize()
+    assert torch.equal(view, ref)
+    assert torch.all(big[:, :, 0] == 7) and torch.all(big[:, :, 155:] == 7)
+
+
 def test_fwd_rejects_other_tile_widths():
     from paper_2312_00229_gb300 import binding as B
     x = torch.zeros(3, 8, 8, dtype=torch.uint8, device=DEV)
     o = torch.zeros(3, 16, 16, dtype=torch.uint8, device=DEV)
-    for tw in (1, 118, 120, 246, 248, 256, -1):
+    for tw in (1, 117, 120, 245, 248, 256, -1):
         rc = B.weno_zoom2x_fwd_tiled(api.image(x), 0, api.image(o), 0, api.Params().c(), 0, tw,
                                      api._stream(x.device))
         assert rc == B.WENO_EINVAL, tw
