@@ -321,15 +321,18 @@ __global__ void __launch_bounds__(NT1, 3) k_bwd_plus(BwdArgs a, MethodConsts k, 
     __syncthreads();
     R.A[s & 15][u] = cur;
 
+    // Each stage runs only on the rows the band's outputs need (the guards
+    // are uniform across the CTA): the pipeline's fill and drain steps do
+    // just the stages that have work.
     // ---- x indicators, row s-3 ----
-    {
+    if (s - 3 >= a0 - 5 && s - 3 <= a1 + 4) {
       const int ra = s - 3;
       const Sten q = sten_x(R.A[(ra - 1) & 15] + u, R.A[ra & 15] + u, R.A[(ra + 1) & 15] + u,
                             R.A[(ra + 2) & 15] + u);
       R.SIX[ra & 3][u] = indicators(q, k.kappa1, k.eps1);
     }
     // ---- x values, row s-5 ----
-    {
+    if (s - 5 >= a0 - 4 && s - 5 <= a1 + 3) {
       const int ra = s - 5;
       float D[4], om[4];
       smooth(R.SIX[ra & 3][u], R.SIX[(ra - 1) & 3][u], R.SIX[(ra + 1) & 3][u],
@@ -343,7 +346,7 @@ __global__ void __launch_bounds__(NT1, 3) k_bwd_plus(BwdArgs a, MethodConsts k, 
       R.X[ra & 15][u] = x;
     }
     // ---- "+" indicators, row s-7 ----
-    {
+    if (s - 7 >= a0 - 3 && s - 7 <= a1 + 2) {
       const int r = s - 7;
       const Sten qe = sten_e(R.A[r & 15] + u, R.X[(r - 2) & 15][u], R.X[(r - 1) & 15][u],
                              R.X[r & 15][u], R.X[(r + 1) & 15][u]);
@@ -354,7 +357,7 @@ __global__ void __launch_bounds__(NT1, 3) k_bwd_plus(BwdArgs a, MethodConsts k, 
     }
     // ---- "+" adjoints, row s-9 ----
     float4 pe0 = make_float4(0.f, 0.f, 0.f, 0.f), ps0 = pe0;
-    {
+    if (s - 9 >= a0 - 2 && s - 9 <= a1 + 1) {
       const int r = s - 9;
       float4 de = pe0, ds = pe0;
       if (ue_s != 0.f) {
@@ -381,51 +384,54 @@ __global__ void __launch_bounds__(NT1, 3) k_bwd_plus(BwdArgs a, MethodConsts k, 
     // ---- "+" coefficients, row r = s-11 ----
     {
       const int r = s - 11;
+      const bool live = r >= a0 - 2 && r <= a1 + 1;
       // E(r,c) is read by S(r,c), S(r,c+1), S(r-1,c), S(r-1,c+1)
       float sb[4];
-      float4 eh = make_float4(0.f, 0.f, 0.f, 0.f);
-      {
-        smooth(R.DE[r & 3][u], R.DS[r & 3][u], R.DS[r & 3][u + 1], R.DS[(r - 1) & 3][u],
-               R.DS[(r - 1) & 3][u + 1], w, sb);
-        const float4 pb = pe2;
-        if ((pb.x != 0.f || pb.y != 0.f || pb.z != 0.f || pb.w != 0.f) ||
-            (sb[0] != 0.f || sb[1] != 0.f || sb[2] != 0.f || sb[3] != 0.f)) {
-          const Sten q = sten_e(R.A[r & 15] + u, R.X[(r - 2) & 15][u], R.X[(r - 1) & 15][u],
-                                R.X[r & 15][u], R.X[(r + 1) & 15][u]);
-          float cf[4][3];
-          node_coefs(q, pb, sb, k2, cf);
-          // along row r (samples): targets columns c-1, c, c+1, c+2
-          eh = make_float4(cf[1][2], cf[0][0] + cf[1][1], cf[0][1] + cf[1][0], cf[0][2]);
-          // along column c (x values): rows r-2 .. r+1
-          xacc[0] += cf[3][2];
-          xacc[1] += cf[2][0] + cf[3][1];
-          xacc[2] += cf[2][1] + cf[3][0];
-          xacc[3] += cf[2][2];
+      if (live) {
+        float4 eh = make_float4(0.f, 0.f, 0.f, 0.f);
+        {
+          smooth(R.DE[r & 3][u], R.DS[r & 3][u], R.DS[r & 3][u + 1], R.DS[(r - 1) & 3][u],
+                 R.DS[(r - 1) & 3][u + 1], w, sb);
+          const float4 pb = pe2;
+          if ((pb.x != 0.f || pb.y != 0.f || pb.z != 0.f || pb.w != 0.f) ||
+              (sb[0] != 0.f || sb[1] != 0.f || sb[2] != 0.f || sb[3] != 0.f)) {
+            const Sten q = sten_e(R.A[r & 15] + u, R.X[(r - 2) & 15][u], R.X[(r - 1) & 15][u],
+                                  R.X[r & 15][u], R.X[(r + 1) & 15][u]);
+            float cf[4][3];
+            node_coefs(q, pb, sb, k2, cf);
+            // along row r (samples): targets columns c-1, c, c+1, c+2
+            eh = make_float4(cf[1][2], cf[0][0] + cf[1][1], cf[0][1] + cf[1][0], cf[0][2]);
+            // along column c (x values): rows r-2 .. r+1
+            xacc[0] += cf[3][2];
+            xacc[1] += cf[2][0] + cf[3][1];
+            xacc[2] += cf[2][1] + cf[3][0];
+            xacc[3] += cf[2][2];
+          }
         }
-      }
-      R.EH[r & 1][u] = eh;
-      // S(r,c) is read by E(r,c), E(r+1,c), E(r,c-1), E(r+1,c-1)
-      float4 sh = make_float4(0.f, 0.f, 0.f, 0.f);
-      {
-        smooth(R.DS[r & 3][u], R.DE[r & 3][u], R.DE[(r + 1) & 3][u], R.DE[r & 3][u - 1],
-               R.DE[(r + 1) & 3][u - 1], w, sb);
-        const float4 pb = ps2;
-        if ((pb.x != 0.f || pb.y != 0.f || pb.z != 0.f || pb.w != 0.f) ||
-            (sb[0] != 0.f || sb[1] != 0.f || sb[2] != 0.f || sb[3] != 0.f)) {
-          const Sten q = sten_s(R.X[r & 15] + u, R.A[(r - 1) & 15][u], R.A[r & 15][u],
-                                R.A[(r + 1) & 15][u], R.A[(r + 2) & 15][u]);
-          float cf[4][3];
-          node_coefs(q, pb, sb, k2, cf);
-          // along row r (x values): targets columns c-2, c-1, c, c+1
-          sh = make_float4(cf[1][2], cf[0][0] + cf[1][1], cf[0][1] + cf[1][0], cf[0][2]);
-          // along column c (samples): rows r-1 .. r+2
-          aacc[0] += cf[3][2];
-          aacc[1] += cf[2][0] + cf[3][1];
-          aacc[2] += cf[2][1] + cf[3][0];
-          aacc[3] += cf[2][2];
+        R.EH[r & 1][u] = eh;
+        // S(r,c) is read by E(r,c), E(r+1,c), E(r,c-1), E(r+1,c-1)
+        float4 sh = make_float4(0.f, 0.f, 0.f, 0.f);
+        {
+          smooth(R.DS[r & 3][u], R.DE[r & 3][u], R.DE[(r + 1) & 3][u], R.DE[r & 3][u - 1],
+                 R.DE[(r + 1) & 3][u - 1], w, sb);
+          const float4 pb = ps2;
+          if ((pb.x != 0.f || pb.y != 0.f || pb.z != 0.f || pb.w != 0.f) ||
+              (sb[0] != 0.f || sb[1] != 0.f || sb[2] != 0.f || sb[3] != 0.f)) {
+            const Sten q = sten_s(R.X[r & 15] + u, R.A[(r - 1) & 15][u], R.A[r & 15][u],
+                                  R.A[(r + 1) & 15][u], R.A[(r + 2) & 15][u]);
+            float cf[4][3];
+            node_coefs(q, pb, sb, k2, cf);
+            // along row r (x values): targets columns c-2, c-1, c, c+1
+            sh = make_float4(cf[1][2], cf[0][0] + cf[1][1], cf[0][1] + cf[1][0], cf[0][2]);
+            // along column c (samples): rows r-1 .. r+2
+            aacc[0] += cf[3][2];
+            aacc[1] += cf[2][0] + cf[3][1];
+            aacc[2] += cf[2][1] + cf[3][0];
+            aacc[3] += cf[2][2];
+          }
         }
+        R.SH[r & 3][u] = sh;
       }
-      R.SH[r & 3][u] = sh;
 
       // ---- X_bar of row r-2 and the partial A_bar of row r-1 are complete ----
       const int q = r - 2, p = r - 1;
@@ -508,15 +514,16 @@ __global__ void __launch_bounds__(NT2, 3) k_bwd_cross(BwdArgs a, MethodConsts k,
       a.gin[plane * a.gi_sc + (int64_t)emitted * a.gi_sh + (int64_t)c * a.gi_sw] = v;
     }
 
+    // Stages run only on the rows the band's outputs need (uniform guards).
     // ---- x indicators, row s-3 ----
-    {
+    if (s - 3 >= a0 - 4 && s - 3 <= a1 + 2) {
       const int ra = s - 3;
       const Sten q = sten_x(R.A[(ra - 1) & 15] + u, R.A[ra & 15] + u, R.A[(ra + 1) & 15] + u,
                             R.A[(ra + 2) & 15] + u);
       R.SIX[ra & 3][u] = indicators(q, k.kappa1, k.eps1);
     }
     // ---- x adjoints, row s-5 ----
-    {
+    if (s - 5 >= a0 - 3 && s - 5 <= a1 + 1) {
       const int ra = s - 5;
       const float xb = xb_s;
       float4 px = make_float4(0.f, 0.f, 0.f, 0.f), dx = px;
@@ -532,7 +539,7 @@ __global__ void __launch_bounds__(NT2, 3) k_bwd_cross(BwdArgs a, MethodConsts k,
       R.DX[ra & 3][u] = dx;
     }
     // ---- x coefficients, row s-7 ----
-    {
+    if (s - 7 >= a0 - 2 && s - 7 <= a1) {
       const int ra = s - 7;
       float sb[4];
       smooth(R.DX[ra & 3][u], R.DX[(ra - 1) & 3][u], R.DX[(ra + 1) & 3][u],
@@ -559,7 +566,7 @@ __global__ void __launch_bounds__(NT2, 3) k_bwd_cross(BwdArgs a, MethodConsts k,
       R.CM[ra & 1][u] = cm;
     }
     // ---- contributions of x row s-8 from the neighbouring columns ----
-    {
+    if (s - 8 >= a0 - 2 && s - 8 <= a1) {
       const int rp = s - 8;
       const float2 c1 = R.C1[rp & 1][u - 1];  // from column c-1: rows rp, rp+1
       const float2 c2 = R.C2[rp & 1][u - 2];  // from column c-2: rows rp+2, rp-1
@@ -629,12 +636,12 @@ cudaError_t launch_all(const BwdArgs& a, const MethodConsts& k, cudaStream_t st)
   // k_bwd_plus: the extended grid, rows and columns [-2, n+2) x [-2, m+2)
   const int64_t ext_n = a.n + 2 * BWD_GHOST, ext_m = a.m + 2 * BWD_GHOST;
   const int64_t sx1 = (ext_m + TW1 - 1) / TW1;
-  const int h1 = band_rows(ext_n, sx1 * a.planes, 19, occ1 * sms);
+  const int h1 = band_rows(ext_n, sx1 * a.planes, 10, occ1 * sms);
   const dim3 g1((unsigned)sx1, (unsigned)((ext_n + h1 - 1) / h1), (unsigned)a.planes);
   k_bwd_plus<BMODE><<<g1, NT1, sm1, st>>>(a, k, h1);
   // k_bwd_cross: image rows and columns, ghosts folded at the edges
   const int64_t sx2 = (a.m + TW2 - 1) / TW2;
-  const int h2 = band_rows(a.n, sx2 * a.planes, 15, occ2 * sms);
+  const int h2 = band_rows(a.n, sx2 * a.planes, 8, occ2 * sms);
   const dim3 g2((unsigned)sx2, (unsigned)((a.n + h2 - 1) / h2), (unsigned)a.planes);
   k_bwd_cross<BMODE><<<g2, NT2, sm2, st>>>(a, k, h2);
   return cudaGetLastError();
