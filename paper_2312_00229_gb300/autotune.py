@@ -31,7 +31,7 @@ CANDIDATES = (0, 16, 24, 32, 48, 64, 96, 128, 192)
 # output columns per CTA: one column per thread (256 and 128 threads) and
 # two columns per thread (128 and 64 threads)
 TILE_WIDTHS = (247, 119, 246, 118)
-BATCHED_TILE_WIDTHS = (247, 119)  # the persistent kernel runs the one-column tile
+BATCHED_TILE_WIDTHS = TILE_WIDTHS  # the persistent kernel runs either tile
 
 _lock = threading.Lock()
 _cache: Optional[Dict[str, int]] = None

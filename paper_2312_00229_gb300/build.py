@@ -18,7 +18,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libwdweno.so")
-SOURCES = ["wd_api.cu", "wd_fwd.cu", "wd_fwd_typed.cu", "wd_batched.cu", "wd_bwd.cu",
+SOURCES = ["wd_api.cu", "wd_fwd.cu", "wd_fwd_typed.cu", "wd_fwd_typed_b2r.cu", "wd_batched.cu",
+           "wd_batched2.cu", "wd_bwd.cu",
            "wd_resample.cu", "wd_noalloc.cu", "wd_cascade.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

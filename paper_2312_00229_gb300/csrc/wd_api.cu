@@ -407,14 +407,14 @@ int weno_zoom2x_batched(int count, const weno_image* d_in, weno_dtype in_t,
   if (reinterpret_cast<uintptr_t>(workspace) % 16 != 0) return WENO_EWORKSPACE;
   if (rows_per_tile < 0 || rows_per_tile > 4096) return WENO_EINVAL;
   int threads = threads_fwd(), cols = 1;
-  if (tile_width != 0 && (!shape_for_width(tile_width, &threads, &cols) || cols != 1))
-    return WENO_EINVAL;  // the persistent kernel runs the one-column tile
+  if (tile_width != 0 && !shape_for_width(tile_width, &threads, &cols)) return WENO_EINVAL;
   MethodConsts k;
   int bmode;
   if (!fold_consts(p, &k, &bmode)) return WENO_EINVAL;
   if (bmode == B2 && direct_b2_ok(p, in_t)) bmode = B2R;
   BatchedArgs a;
   a.threads = threads;
+  a.cols = cols;
   a.count = count;
   a.in = d_in;
   a.out = d_out;

@@ -16,7 +16,8 @@ struct BatchedArgs {
   const weno_image* out;  // device array
   int in_dtype, out_dtype, out_mode;
   int64_t rows_per_band;
-  int threads;            // CTA width: 256 or 128
+  int threads;            // CTA width: 256 or 128 (one column per thread), 128 or 64 (two)
+  int cols;               // coarse columns per thread: 1 or 2
   void* workspace;        // >= batched_workspace_bytes(count), 16-byte aligned
 };
 

@@ -6,23 +6,18 @@
 
 namespace wdweno {
 
+// The direct 1/D^2 weights (B2R) are in wd_fwd_typed_b2r.cu (compiled in
+// parallel).
+cudaError_t launch_fwd_typed_b2r(const FwdArgs& a, const MethodConsts& k, cudaStream_t stream,
+                                 bool* handled);
+
 cudaError_t launch_fwd_typed(const FwdArgs& a, const MethodConsts& k, int bmode,
                              cudaStream_t stream, bool* handled) {
   using fwd_kernels::launch_fwd;
   using fwd_tile::TypedIO;
   *handled = true;
   const int i = a.in_dtype, o = a.out_dtype;
-  if (bmode == B2R) {  // data bounded by the storage type or the caller's bound
-    if (i == DT_U8 && o == DT_U8) return launch_fwd<B2R, TypedIO<uint8_t, uint8_t>>(a, k, stream);
-    if (i == DT_F16 && o == DT_F16) return launch_fwd<B2R, TypedIO<__half, __half>>(a, k, stream);
-    if (i == DT_U8 && o == DT_F32) return launch_fwd<B2R, TypedIO<uint8_t, float>>(a, k, stream);
-    if (i == DT_F32 && o == DT_F32) return launch_fwd<B2R, TypedIO<float, float>>(a, k, stream);
-    if (i == DT_F32 && o == DT_U8) return launch_fwd<B2R, TypedIO<float, uint8_t>>(a, k, stream);
-    if (i == DT_BF16 && o == DT_BF16)
-      return launch_fwd<B2R, TypedIO<__nv_bfloat16, __nv_bfloat16>>(a, k, stream);
-    *handled = false;
-    return cudaSuccess;
-  }
+  if (bmode == B2R) return launch_fwd_typed_b2r(a, k, stream, handled);
   if (i == DT_U8 && o == DT_U8) return launch_fwd<B2, TypedIO<uint8_t, uint8_t>>(a, k, stream);
   if (i == DT_F16 && o == DT_F16) return launch_fwd<B2, TypedIO<__half, __half>>(a, k, stream);
   if (i == DT_BF16 && o == DT_BF16)

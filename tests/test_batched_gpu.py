@@ -145,19 +145,21 @@ def test_batched_fp32_with_data_bound():
 
 
 @pytest.mark.parametrize("dtype", [torch.uint8, torch.float16, torch.float32])
-def test_batched_narrow_ctas(dtype):
-    """The persistent launch with 128-thread CTAs (tile width 119) equals the
-    single-image kernel bit for bit for every image, edge sizes included."""
+@pytest.mark.parametrize("tw", [119, 246, 118])
+def test_batched_other_tile_shapes(dtype, tw):
+    """The persistent launch with 128-thread CTAs (tile width 119) or two
+    columns per thread (246: 128 threads, 118: 64) equals the single-image
+    kernel bit for bit for every image, edge sizes included."""
     imgs = _images(dtype, SIZES, seed=17)
     for rows in (0, 32):
-        outs = api.BatchedPlan(imgs, rows_per_tile=rows, tile_width=119).run()
+        outs = api.BatchedPlan(imgs, rows_per_tile=rows, tile_width=tw).run()
         singles = [api.zoom2x_fwd(x) for x in imgs]
         torch.cuda.synchronize()
         for x, o, s in zip(imgs, outs, singles):
-            assert torch.equal(o, s), (tuple(x.shape), rows)
+            assert torch.equal(o, s), (tuple(x.shape), rows, tw)
     from paper_2312_00229_gb300 import binding as B
     plan = api.BatchedPlan(imgs[:2])
-    for tw in (1, 118, 120, 256):
+    for tw in (1, 117, 120, 256):
         rc = B.weno_zoom2x_batched(2, ctypes.c_void_p(plan.d_in.data_ptr()), plan.in_t,
                                    ctypes.c_void_p(plan.d_out.data_ptr()), plan.out_t,
                                    plan.params.c(), ctypes.c_void_p(plan.workspace.data_ptr()),

@@ -132,7 +132,7 @@ def test_batched_rejects_bad_arguments_without_launching():
     assert B.weno_zoom2x_batched(3, 1, 0, 1, 0, p, None, need, 0, 0, None) == B.WENO_EWORKSPACE
     assert B.weno_zoom2x_batched(3, 1, 0, 1, 0, p, 0x100, need - 16, 0, 0,
                                  None) == B.WENO_EWORKSPACE
-    for tw in (-1, 1, 77, 118, 120, 128, 246, 248, 256):  # widths other than 0, 247, 119
+    for tw in (-1, 1, 77, 117, 120, 128, 245, 248, 256):  # widths other than 0, 247, 119, 246, 118
         assert B.weno_zoom2x_batched(3, 1, 0, 1, 0, p, 0x100, need, 0, tw,
                                      None) == B.WENO_EINVAL
     assert B.weno_zoom2x_batched(3, 1, 0, 1, 0, p, 0x100, need, 4097, 0, None) == B.WENO_EINVAL
