@@ -61,8 +61,11 @@ struct RingsPlus {
   float4 SIS[4][W];   // S-point indicators
   float4 DE[4][W];    // E D_bar
   float4 DS[4][W];    // S D_bar
-  float4 EH[2][W];    // E along-row stencils: node contributions to columns c-1..c+2
-  float4 SH[4][W];    // S along-row stencils: contributions to x columns c-2..c+1
+  // Row stencils' node contributions pre-summed by target column, one array
+  // per target so that each gather reads a scalar per thread (no strided
+  // component reads of a vector array)
+  float EH[4][2][W];  // E along row r: to sample columns c-1, c, c+1, c+2
+  float SH[4][4][W];  // S along row r: to x columns c-2, c-1, c, c+1
 };
 
 template <int NT>
@@ -388,7 +391,7 @@ __global__ void __launch_bounds__(NT1, 3) k_bwd_plus(BwdArgs a, MethodConsts k, 
       // E(r,c) is read by S(r,c), S(r,c+1), S(r-1,c), S(r-1,c+1)
       float sb[4];
       if (live) {
-        float4 eh = make_float4(0.f, 0.f, 0.f, 0.f);
+        float eh[4] = {0.f, 0.f, 0.f, 0.f};
         {
           smooth(R.DE[r & 3][u], R.DS[r & 3][u], R.DS[r & 3][u + 1], R.DS[(r - 1) & 3][u],
                  R.DS[(r - 1) & 3][u + 1], w, sb);
@@ -400,7 +403,10 @@ __global__ void __launch_bounds__(NT1, 3) k_bwd_plus(BwdArgs a, MethodConsts k, 
             float cf[4][3];
             node_coefs(q, pb, sb, k2, cf);
             // along row r (samples): targets columns c-1, c, c+1, c+2
-            eh = make_float4(cf[1][2], cf[0][0] + cf[1][1], cf[0][1] + cf[1][0], cf[0][2]);
+            eh[0] = cf[1][2];
+            eh[1] = cf[0][0] + cf[1][1];
+            eh[2] = cf[0][1] + cf[1][0];
+            eh[3] = cf[0][2];
             // along column c (x values): rows r-2 .. r+1
             xacc[0] += cf[3][2];
             xacc[1] += cf[2][0] + cf[3][1];
@@ -408,9 +414,10 @@ __global__ void __launch_bounds__(NT1, 3) k_bwd_plus(BwdArgs a, MethodConsts k, 
             xacc[3] += cf[2][2];
           }
         }
-        R.EH[r & 1][u] = eh;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) R.EH[j][r & 1][u] = eh[j];
         // S(r,c) is read by E(r,c), E(r+1,c), E(r,c-1), E(r+1,c-1)
-        float4 sh = make_float4(0.f, 0.f, 0.f, 0.f);
+        float sh[4] = {0.f, 0.f, 0.f, 0.f};
         {
           smooth(R.DS[r & 3][u], R.DE[r & 3][u], R.DE[(r + 1) & 3][u], R.DE[r & 3][u - 1],
                  R.DE[(r + 1) & 3][u - 1], w, sb);
@@ -422,7 +429,10 @@ __global__ void __launch_bounds__(NT1, 3) k_bwd_plus(BwdArgs a, MethodConsts k, 
             float cf[4][3];
             node_coefs(q, pb, sb, k2, cf);
             // along row r (x values): targets columns c-2, c-1, c, c+1
-            sh = make_float4(cf[1][2], cf[0][0] + cf[1][1], cf[0][1] + cf[1][0], cf[0][2]);
+            sh[0] = cf[1][2];
+            sh[1] = cf[0][0] + cf[1][1];
+            sh[2] = cf[0][1] + cf[1][0];
+            sh[3] = cf[0][2];
             // along column c (samples): rows r-1 .. r+2
             aacc[0] += cf[3][2];
             aacc[1] += cf[2][0] + cf[3][1];
@@ -430,15 +440,16 @@ __global__ void __launch_bounds__(NT1, 3) k_bwd_plus(BwdArgs a, MethodConsts k, 
             aacc[3] += cf[2][2];
           }
         }
-        R.SH[r & 3][u] = sh;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) R.SH[j][r & 3][u] = sh[j];
       }
 
       // ---- X_bar of row r-2 and the partial A_bar of row r-1 are complete ----
       const int q = r - 2, p = r - 1;
-      const float4* shq = R.SH[q & 3] + u;
-      const float4* ehp = R.EH[p & 1] + u;
-      const float xb = xacc[0] + (shq[2].x + shq[1].y) + (shq[0].z + shq[-1].w) + gx_s;
-      const float ab = aacc[0] + (ehp[1].x + ehp[0].y) + (ehp[-1].z + ehp[-2].w) + ga_s;
+      const float xb = xacc[0] + (R.SH[0][q & 3][u + 2] + R.SH[1][q & 3][u + 1]) +
+                       (R.SH[2][q & 3][u] + R.SH[3][q & 3][u - 1]) + gx_s;
+      const float ab = aacc[0] + (R.EH[0][p & 1][u + 1] + R.EH[1][p & 1][u]) +
+                       (R.EH[2][p & 1][u - 1] + R.EH[3][p & 1][u - 2]) + ga_s;
       if (col_out && q >= a0 && q < a1) ws.xb[ws.idx(q, c)] = xb;
       if (col_out && p >= a0 && p < a1) ws.ab[ws.idx(p, c)] = ab;
       xacc[0] = xacc[1]; xacc[1] = xacc[2]; xacc[2] = xacc[3]; xacc[3] = 0.f;
