@@ -45,10 +45,12 @@ constexpr int PAD = 2;  // ring columns before / after the CTA's threads
 
 // k_bwd_plus: thread t owns column c = b0 - HL1 + t of a strip whose outputs
 // are columns [b0, b0 + NT - HL1 - HR1) of the extended grid.
-constexpr int NT1 = 128, HL1 = 6, HR1 = 7, TW1 = NT1 - HL1 - HR1;
-// k_bwd_cross: the strip's outputs are image columns [b0, b0 + TW2) plus,
-// at the image edges, the ghost columns folded onto them.
-constexpr int NT2 = 128, HL2 = 10, HR2 = 10, TW2 = NT2 - HL2 - HR2;
+constexpr int HL1 = 6, HR1 = 7;
+// k_bwd_cross: the strip's outputs are image columns [b0, b0 + NT - HL2 - HR2)
+// plus, at the image edges, the ghost columns folded onto them.
+constexpr int HL2 = 10, HR2 = 10;
+// CTA widths built for both sweeps (the host picks one per image width)
+constexpr int NT_NARROW = 128, NT_WIDE = 192;
 constexpr int GA = 5;  // ghost rows / columns of A_bar (nonzero up to 4)
 
 template <int NT>
@@ -275,8 +277,10 @@ __device__ __forceinline__ GCol gcol(const BwdArgs& a, int64_t plane, int64_t Q)
 // Lags (row = s - L at step s): input row 0, x indicators 3, x values 5,
 // "+" indicators 7, "+" adjoints 9, "+" coefficients 11; the partial A_bar of
 // row s - 12 and X_bar of row s - 13 are complete at the end of step s.
-template <int BMODE>
-__global__ void __launch_bounds__(NT1, 3) k_bwd_plus(BwdArgs a, MethodConsts k, int rows) {
+template <int BMODE, int NT1>
+__global__ void __launch_bounds__(NT1, NT1 == NT_NARROW ? 3 : 2)
+    k_bwd_plus(BwdArgs a, MethodConsts k, int rows) {
+  constexpr int TW1 = NT1 - HL1 - HR1;
   extern __shared__ __align__(16) unsigned char smem[];
   RingsPlus<NT1>& R = *reinterpret_cast<RingsPlus<NT1>*>(smem);
   const int t = threadIdx.x;
@@ -463,8 +467,9 @@ __global__ void __launch_bounds__(NT1, 3) k_bwd_plus(BwdArgs a, MethodConsts k, 
 // ---- k_bwd_cross ---------------------------------------------------------------
 // Lags: input row 0, x indicators 3, x adjoints 5, x coefficients 7; A_bar
 // of row s - 9 is complete at step s and written (column-folded) at s + 1.
-template <int BMODE>
+template <int BMODE, int NT2>
 __global__ void __launch_bounds__(NT2, 3) k_bwd_cross(BwdArgs a, MethodConsts k, int rows) {
+  constexpr int TW2 = NT2 - HL2 - HR2;
   extern __shared__ __align__(16) unsigned char smem[];
   RingsCross<NT2>& R = *reinterpret_cast<RingsCross<NT2>*>(smem);
   const int t = threadIdx.x;
@@ -624,37 +629,75 @@ int band_rows(int64_t rows_total, int64_t ctas_per_band_row, int fill, int resid
   return best;
 }
 
-template <int BMODE>
-cudaError_t launch_all(const BwdArgs& a, const MethodConsts& k, cudaStream_t st) {
-  const size_t sm1 = sizeof(RingsPlus<NT1>), sm2 = sizeof(RingsCross<NT2>);
-  cudaError_t e = cudaFuncSetAttribute(k_bwd_plus<BMODE>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_bwd_cross<BMODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)sm2);
-  if (e != cudaSuccess) return e;
-  int dev = 0, sms = 0, occ1 = 0, occ2 = 0;
+// One sweep kernel with the CTA width, of NT_NARROW and NT_WIDE, that
+// spends the least: for each width, the band height band_rows chooses, then
+// the per-SM work ceil(CTAs / SMs) x threads x (rows per band + fill).
+struct SweepShape {
+  const void* fn;
+  size_t smem;
+  int threads, occ, strips, rows;
+  int64_t bands;
+};
+
+template <class KN, class KW>
+cudaError_t pick_shape(KN kn, KW kw, size_t smem_n, size_t smem_w, int tw_n, int tw_w,
+                       int64_t rows_total, int64_t cols_total, int64_t planes, int fill,
+                       SweepShape* best) {
+  int dev = 0, sms = 0;
+  cudaError_t e;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
     return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, k_bwd_plus<BMODE>, NT1, sm1)) !=
-      cudaSuccess)
-    return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, k_bwd_cross<BMODE>, NT2, sm2)) !=
-      cudaSuccess)
-    return e;
-  if (occ1 < 1 || occ2 < 1) return cudaErrorInvalidConfiguration;
+  const void* fns[2] = {(const void*)kn, (const void*)kw};
+  const size_t smems[2] = {smem_n, smem_w};
+  const int nts[2] = {NT_NARROW, NT_WIDE}, tws[2] = {tw_n, tw_w};
+  double best_cost = -1.0;
+  for (int i = 0; i < 2; ++i) {
+    if ((e = cudaFuncSetAttribute(fns[i], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smems[i])) != cudaSuccess)
+      return e;
+    int occ = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fns[i], nts[i], smems[i])) !=
+        cudaSuccess)
+      return e;
+    if (occ < 1) continue;
+    const int64_t strips = (cols_total + tws[i] - 1) / tws[i];
+    const int h = band_rows(rows_total, strips * planes, fill, occ * sms);
+    const int64_t bands = (rows_total + h - 1) / h;
+    const int64_t per_sm = (strips * bands * planes + sms - 1) / sms;
+    const double cost = double(per_sm) * nts[i] * double(h + fill);
+    if (best_cost < 0.0 || cost < best_cost) {
+      best_cost = cost;
+      *best = SweepShape{fns[i], smems[i], nts[i], occ, (int)strips, h, bands};
+    }
+  }
+  return best_cost < 0.0 ? cudaErrorInvalidConfiguration : cudaSuccess;
+}
+
+template <int BMODE>
+cudaError_t launch_all(const BwdArgs& a, const MethodConsts& k, cudaStream_t st) {
   // k_bwd_plus: the extended grid, rows and columns [-2, n+2) x [-2, m+2)
-  const int64_t ext_n = a.n + 2 * BWD_GHOST, ext_m = a.m + 2 * BWD_GHOST;
-  const int64_t sx1 = (ext_m + TW1 - 1) / TW1;
-  const int h1 = band_rows(ext_n, sx1 * a.planes, 10, occ1 * sms);
-  const dim3 g1((unsigned)sx1, (unsigned)((ext_n + h1 - 1) / h1), (unsigned)a.planes);
-  k_bwd_plus<BMODE><<<g1, NT1, sm1, st>>>(a, k, h1);
+  SweepShape s1, s2;
+  cudaError_t e = pick_shape(k_bwd_plus<BMODE, NT_NARROW>, k_bwd_plus<BMODE, NT_WIDE>,
+                             sizeof(RingsPlus<NT_NARROW>), sizeof(RingsPlus<NT_WIDE>),
+                             NT_NARROW - HL1 - HR1, NT_WIDE - HL1 - HR1,
+                             a.n + 2 * BWD_GHOST, a.m + 2 * BWD_GHOST, a.planes, 10, &s1);
+  if (e != cudaSuccess) return e;
+  const dim3 g1((unsigned)s1.strips, (unsigned)s1.bands, (unsigned)a.planes);
+  if (s1.threads == NT_WIDE)
+    k_bwd_plus<BMODE, NT_WIDE><<<g1, NT_WIDE, s1.smem, st>>>(a, k, s1.rows);
+  else
+    k_bwd_plus<BMODE, NT_NARROW><<<g1, NT_NARROW, s1.smem, st>>>(a, k, s1.rows);
   // k_bwd_cross: image rows and columns, ghosts folded at the edges
-  const int64_t sx2 = (a.m + TW2 - 1) / TW2;
-  const int h2 = band_rows(a.n, sx2 * a.planes, 8, occ2 * sms);
-  const dim3 g2((unsigned)sx2, (unsigned)((a.n + h2 - 1) / h2), (unsigned)a.planes);
-  k_bwd_cross<BMODE><<<g2, NT2, sm2, st>>>(a, k, h2);
+  e = pick_shape(k_bwd_cross<BMODE, NT_NARROW>, k_bwd_cross<BMODE, NT_WIDE>,
+                 sizeof(RingsCross<NT_NARROW>), sizeof(RingsCross<NT_WIDE>),
+                 NT_NARROW - HL2 - HR2, NT_WIDE - HL2 - HR2, a.n, a.m, a.planes, 8, &s2);
+  if (e != cudaSuccess) return e;
+  const dim3 g2((unsigned)s2.strips, (unsigned)s2.bands, (unsigned)a.planes);
+  if (s2.threads == NT_WIDE)
+    k_bwd_cross<BMODE, NT_WIDE><<<g2, NT_WIDE, s2.smem, st>>>(a, k, s2.rows);
+  else
+    k_bwd_cross<BMODE, NT_NARROW><<<g2, NT_NARROW, s2.smem, st>>>(a, k, s2.rows);
   return cudaGetLastError();
 }
 
