@@ -129,6 +129,29 @@ def tune_fwd(x: torch.Tensor, params=None, out_dtype=None, layout: str = "chw",
 
 
 
+def tune_cascade(x: torch.Tensor, levels: int, params=None, out_dtype=None,
+                 inter_dtype=torch.float32, layout: str = "chw",
+                 candidates: Iterable[int] = CANDIDATES, reps: int = 10) -> list:
+    """Tunes the tile shape of every level of ``api.cascade_zoom(x, levels)``
+    (each level is its own size class: its input shape and storage pair),
+    running the chain on `x` to get each level's input.  Returns the
+    per-level timing dicts of ``tune_fwd``."""
+    import dataclasses
+
+    from . import api
+    params = params or api.Params()
+    bounds = api._level_bounds(x, params, levels)
+    cur, out = x, []
+    for lvl in range(levels):
+        last = lvl == levels - 1
+        p = dataclasses.replace(params, h=params.h / (1 << lvl), data_bound=bounds[lvl])
+        odt = (out_dtype or x.dtype) if last else inter_dtype
+        out.append(tune_fwd(cur, p, out_dtype=odt, layout=layout, candidates=candidates,
+                            reps=reps))
+        cur = api.zoom2x_fwd(cur, p, out_dtype=odt, layout=layout)
+    return out
+
+
 def _batched_key(images: Sequence[torch.Tensor], out_dtype, layout: str) -> str:
     return "|".join(["batched", _device_name(images[0].device),
                      str(images[0].dtype), str(out_dtype or images[0].dtype), layout,

@@ -43,3 +43,16 @@ def test_tune_batched_caches_a_shape_that_keeps_the_outputs(fresh_cache):
     torch.cuda.synchronize()
     for a, b in zip(got, want):
         assert torch.equal(a, b)
+
+
+def test_tune_cascade_keeps_every_output_bit(fresh_cache):
+    """Tuning each level of a cascade caches a shape per level's size class;
+    the cascade then runs with them and gives the same bits."""
+    g = torch.Generator(device=DEV).manual_seed(22)
+    x = torch.randint(0, 256, (3, 70, 90), device=DEV, generator=g, dtype=torch.uint8)
+    want = api.cascade_zoom(x, 3)  # library default shapes (empty cache)
+    times = autotune.tune_cascade(x, 3, candidates=(0, 16, 64), reps=2)
+    assert len(times) == 3 and all(len(t) == 3 * 5 for t in times)
+    got = api.cascade_zoom(x, 3)
+    torch.cuda.synchronize()
+    assert torch.equal(got, want)
