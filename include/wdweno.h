@@ -147,10 +147,11 @@ size_t weno_zoom2x_batched_workspace_bytes(int count);
  *   workspace   : device buffer of >= weno_zoom2x_batched_workspace_bytes
  *                 bytes; contents need no initialisation and are scratch
  *   rows_per_tile, tile_width : tile shape (0 = library default: 128-row
- *                 bands, 247-column strips); tile_width 119 runs 128-thread
- *                 CTAs (a smaller part of each image's last strip idles,
- *                 which pays for narrow images); the autotuner chooses both
- *                 per size class
+ *                 bands, 247-column strips); tile_width takes the values of
+ *                 weno_zoom2x_fwd_tiled (247, 119, 246, 118); narrower
+ *                 strips leave a smaller part of each image's last strip
+ *                 idle, which pays for narrow images; the autotuner chooses
+ *                 both per size class
  * Shapes follow weno_zoom2x_fwd per image; descriptors are read on the
  * device, so a malformed descriptor is skipped (its output is left
  * untouched) rather than reported.
@@ -164,11 +165,14 @@ int weno_zoom2x_batched(int count, const weno_image* d_in, weno_dtype in_t,
  *   rows_per_tile : coarse rows per CTA band, 1..4096 (0 = the default:
  *                   the band count that best balances the last wave of CTAs
  *                   on this GPU against the per-band pipeline fill)
- *   tile_width    : coarse output columns per CTA: 247 (256 threads, one
- *                   column each, 9 of them covering the dependency halo),
- *                   119 (128 threads), or 0 = the library's choice for the
- *                   image width (119 when its strips need no more threads
- *                   across the width than 247-column strips)
+ *   tile_width    : coarse output columns per CTA, which also fixes the
+ *                   coarse columns each thread owns: 247 (256 threads of one
+ *                   column, 9 columns covering the dependency halo), 119
+ *                   (128 threads of one column), 246 (128 threads of two
+ *                   adjacent columns, 10 halo columns), 118 (64 threads of
+ *                   two), or 0 = the library's choice for the image width
+ *                   (the shape that spends the fewest column-steps across
+ *                   it).  Every shape gives bit-identical outputs.
  * Returns as weno_zoom2x_fwd, or WENO_EINVAL for an unsupported shape and
  * WENO_ERANGE when the band count exceeds 65535. */
 int weno_zoom2x_fwd_tiled(const weno_image* in, weno_dtype in_t, const weno_image* out,
