@@ -252,6 +252,85 @@ __device__ __forceinline__ WsPlane ws_plane(const BwdArgs& a, int64_t plane) {
   return w;
 }
 
+// ---- ring addressing of one step ---------------------------------------------
+// A step at row s reads ring rows s - L for lags L known at compile time.
+// RowsRT computes every slot from s at run time (slot = row mod depth);
+// RowsCT<PH> serves the steps s = 4 G + PH of a four-step group: the rows of
+// a 16-row ring fall into four groups of four consecutive slots, whose
+// addresses (RingGroups) are formed once per group of steps, and row s - L
+// lies in group (G - j) mod 4 at position p with j and p compile-time
+// constants; the 4- and 2-row rings' slots are constants.
+template <int W>
+struct RowsRT {
+  float* A;  // row slot 0 of a 16-row ring, at the thread's column
+  float* X;
+  int s;
+  template <int L>
+  __device__ __forceinline__ float* a() const { return A + ((s - L) & 15) * W; }
+  template <int L>
+  __device__ __forceinline__ float* x() const { return X + ((s - L) & 15) * W; }
+  template <int L>
+  __device__ __forceinline__ int m4() const { return (s - L) & 3; }
+  template <int L>
+  __device__ __forceinline__ int m2() const { return (s - L) & 1; }
+};
+
+template <int W>
+struct RingGroups {
+  float* A[4];  // A[j]: first slot of ring group (G - j) mod 4, G = s >> 2
+  float* X[4];
+  __device__ __forceinline__ RingGroups(float* a, float* x, int s) {
+    const int G = s >> 2;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      A[j] = a + 4 * ((G - j) & 3) * W;
+      X[j] = x + 4 * ((G - j) & 3) * W;
+    }
+  }
+};
+
+template <int W, int PH>
+struct RowsCT {
+  const RingGroups<W>& g;
+  template <int L>
+  static constexpr int J = PH >= L ? 0 : (L - PH + 3) / 4;  // groups back
+  template <int L>
+  static constexpr int P = PH - L + 4 * J<L>;  // position inside the group
+  template <int L>
+  __device__ __forceinline__ float* a() const { return g.A[J<L> & 3] + P<L> * W; }
+  template <int L>
+  __device__ __forceinline__ float* x() const { return g.X[J<L> & 3] + P<L> * W; }
+  template <int L>
+  __device__ static constexpr int m4() { return (PH - L) & 3; }
+  template <int L>
+  __device__ static constexpr int m2() { return (PH - L) & 1; }
+};
+
+// Runs a band's steps s_begin .. s_end: four-step groups of FULL steps
+// (every stage live, compile-time slots, no guards) where s is a multiple of
+// 4 and the group lies inside [s_lo, s_hi], generic steps (run-time slots,
+// stage guards) elsewhere.  One instance of each step form.
+template <class SW>
+__device__ __forceinline__ void sweep_band(SW& sw, float* ringA, float* ringX, int s_begin,
+                                           int s_end, int s_lo, int s_hi) {
+  constexpr int W = SW::W;
+  int s = s_begin;
+#pragma unroll 1
+  while (s <= s_end) {
+    if ((s & 3) == 0 && s >= s_lo && s + 3 <= s_hi) {
+      const RingGroups<W> g(ringA, ringX, s);
+      sw.template step<true>(s, RowsCT<W, 0>{g});
+      sw.template step<true>(s + 1, RowsCT<W, 1>{g});
+      sw.template step<true>(s + 2, RowsCT<W, 2>{g});
+      sw.template step<true>(s + 3, RowsCT<W, 3>{g});
+      s += 4;
+    } else {
+      sw.template step<false>(s, RowsRT<W>{ringA, ringX, s});
+      ++s;
+    }
+  }
+}
+
 // ---- k_bwd_plus ----------------------------------------------------------------
 // Output-gradient column of a thread (fine column Q, element pointer at row
 // 0), read row by row.
@@ -260,7 +339,10 @@ struct GCol {
   int64_t sh;
   int orows;
   bool ok;
+  // FULL steps read rows known to lie inside the output
+  template <bool FULL>
   __device__ __forceinline__ float at(int P) const {
+    if (FULL) return ok ? __ldg(p + (int64_t)P * sh) : 0.f;
     return (ok && P >= 0 && P < orows) ? __ldg(p + (int64_t)P * sh) : 0.f;
   }
 };
@@ -274,341 +356,425 @@ __device__ __forceinline__ GCol gcol(const BwdArgs& a, int64_t plane, int64_t Q)
   return g;
 }
 
+__device__ __forceinline__ bool any_nonzero(const float4& v, const float s[4]) {
+  return (v.x != 0.f || v.y != 0.f || v.z != 0.f || v.w != 0.f) ||
+         (s[0] != 0.f || s[1] != 0.f || s[2] != 0.f || s[3] != 0.f);
+}
+
 // Lags (row = s - L at step s): input row 0, x indicators 3, x values 5,
 // "+" indicators 7, "+" adjoints 9, "+" coefficients 11; the partial A_bar of
 // row s - 12 and X_bar of row s - 13 are complete at the end of step s.
+// Guarded steps skip the work of points whose incoming adjoints are all zero
+// (a sparse output gradient); FULL steps do it, with the same result.
 template <int BMODE, int NT1>
-__global__ void __launch_bounds__(NT1, NT1 == NT_NARROW ? 3 : 2)
-    k_bwd_plus(BwdArgs a, MethodConsts k, int rows) {
-  constexpr int TW1 = NT1 - HL1 - HR1;
-  extern __shared__ __align__(16) unsigned char smem[];
-  RingsPlus<NT1>& R = *reinterpret_cast<RingsPlus<NT1>*>(smem);
-  const int t = threadIdx.x;
-  const int64_t plane = blockIdx.z;
-  const int n = (int)a.n, m = (int)a.m;
-  const int b0 = -BWD_GHOST + (int)blockIdx.x * TW1;
-  const int b1 = min(b0 + TW1, m + BWD_GHOST);
-  const int c = b0 - HL1 + t;
-  const int a0 = -BWD_GHOST + (int)blockIdx.y * rows;
-  const int a1 = min(a0 + rows, n + BWD_GHOST);
-  const float* xin = a.x + plane * a.x_sc + (int64_t)clampi(c, 0, m - 1) * a.x_sw;
-  const WsPlane ws = ws_plane(a, plane);
-  const bool col_out = c >= b0 && c < b1;
-  // fine column 2c + 1 (E and x points) and 2c (S points and samples)
-  const GCol godd = gcol(a, plane, 2 * (int64_t)c + 1), gevn = gcol(a, plane, 2 * (int64_t)c);
-  const float w = k.w;
-  const float k2 = k.kappa2 * k.kappa2;
+struct PlusSweep {
+  static constexpr int W = RingsPlus<NT1>::W;
+  RingsPlus<NT1>& R;
+  const MethodConsts k;
+  float w, k2;
+  int u, c, n, a0, a1;
+  const float* xin;
+  int64_t x_sh;
+  WsPlane ws;
+  bool col_out;
+  GCol godd, gevn;  // fine column 2c + 1 (E and x points) and 2c (S points, samples)
+  // carried from step to step
+  float pf, pf2;              // input rows s+1, s+2 of the column
+  float ue, us, gx, ga;       // output gradients of the next step's rows
+  float4 pe1, pe2, ps1, ps2;  // p_bar of the "+" points of rows s-10 (1), s-11 (2)
+  float xacc[4], aacc[4];     // own-column accumulators: X_bar rows r-2 .. r+1,
+                              // A_bar rows r-1 .. r+2 (r = the coefficient row)
 
-  {
-    float* z = reinterpret_cast<float*>(smem);
-    for (int i = t; i < (int)(sizeof(RingsPlus<NT1>) / sizeof(float)); i += NT1) z[i] = 0.f;
+  __device__ __forceinline__ PlusSweep(RingsPlus<NT1>& R_, const BwdArgs& a,
+                                       const MethodConsts& k_, int rows)
+      : R(R_), k(k_) {
+    const int t = threadIdx.x;
+    const int64_t plane = blockIdx.z;
+    constexpr int TW1 = NT1 - HL1 - HR1;
+    n = (int)a.n;
+    const int m = (int)a.m;
+    const int b0 = -BWD_GHOST + (int)blockIdx.x * TW1;
+    const int b1 = min(b0 + TW1, m + BWD_GHOST);
+    c = b0 - HL1 + t;
+    a0 = -BWD_GHOST + (int)blockIdx.y * rows;
+    a1 = min(a0 + rows, n + BWD_GHOST);
+    xin = a.x + plane * a.x_sc + (int64_t)clampi(c, 0, m - 1) * a.x_sw;
+    x_sh = a.x_sh;
+    ws = ws_plane(a, plane);
+    col_out = c >= b0 && c < b1;
+    godd = gcol(a, plane, 2 * (int64_t)c + 1);
+    gevn = gcol(a, plane, 2 * (int64_t)c);
+    w = k.w;
+    k2 = k.kappa2 * k.kappa2;
+    u = t + PAD;
   }
-  const int u = t + PAD;  // this thread's column in the rings
-  const int s_begin = a0 - 6, s_end = a1 - 1 + 13;
-  float pf = __ldg(xin + (int64_t)clampi(s_begin, 0, n - 1) * a.x_sh);
-  float pf2 = __ldg(xin + (int64_t)clampi(s_begin + 1, 0, n - 1) * a.x_sh);
-  // output gradients of the next step's rows, loaded one step ahead
-  float ue = godd.at(2 * (s_begin - 9)), us = gevn.at(2 * (s_begin - 9) + 1);
-  float gx = godd.at(2 * (s_begin - 13) + 1), ga = gevn.at(2 * (s_begin - 12));
-  // p_bar of the "+" points of rows s-10 (1) and s-11 (2), kept by the thread
-  float4 pe1 = make_float4(0.f, 0.f, 0.f, 0.f), pe2 = pe1, ps1 = pe1, ps2 = pe1;
-  // own-column row accumulators: X_bar rows r-2 .. r+1, A_bar rows r-1 .. r+2
-  // (r = the coefficient stage's row)
-  float xacc[4] = {0.f, 0.f, 0.f, 0.f}, aacc[4] = {0.f, 0.f, 0.f, 0.f};
 
-  for (int s = s_begin; s <= s_end; ++s) {
+  template <bool FULL, class SL>
+  __device__ __forceinline__ void step(const int s, const SL& sl) {
     const float cur = pf;
     pf = pf2;
-    pf2 = __ldg(xin + (int64_t)clampi(s + 2, 0, n - 1) * a.x_sh);
+    pf2 = __ldg(xin + (int64_t)clampi(s + 2, 0, n - 1) * x_sh);
     const float ue_s = ue, us_s = us, gx_s = gx, ga_s = ga;
-    ue = godd.at(2 * (s - 8));
-    us = gevn.at(2 * (s - 8) + 1);
-    gx = godd.at(2 * (s - 12) + 1);
-    ga = gevn.at(2 * (s - 11));
+    ue = godd.template at<FULL>(2 * (s - 8));
+    us = gevn.template at<FULL>(2 * (s - 8) + 1);
+    gx = godd.template at<FULL>(2 * (s - 12) + 1);
+    ga = gevn.template at<FULL>(2 * (s - 11));
     __syncthreads();
-    R.A[s & 15][u] = cur;
+    *sl.template a<0>() = cur;
 
     // Each stage runs only on the rows the band's outputs need (the guards
     // are uniform across the CTA): the pipeline's fill and drain steps do
     // just the stages that have work.
     // ---- x indicators, row s-3 ----
-    if (s - 3 >= a0 - 5 && s - 3 <= a1 + 4) {
-      const int ra = s - 3;
-      const Sten q = sten_x(R.A[(ra - 1) & 15] + u, R.A[ra & 15] + u, R.A[(ra + 1) & 15] + u,
-                            R.A[(ra + 2) & 15] + u);
-      R.SIX[ra & 3][u] = indicators(q, k.kappa1, k.eps1);
+    if (FULL || (s - 3 >= a0 - 5 && s - 3 <= a1 + 4)) {
+      const Sten q = sten_x(sl.template a<4>(), sl.template a<3>(), sl.template a<2>(),
+                            sl.template a<1>());
+      R.SIX[sl.template m4<3>()][u] = indicators(q, k.kappa1, k.eps1);
     }
     // ---- x values, row s-5 ----
-    if (s - 5 >= a0 - 4 && s - 5 <= a1 + 3) {
-      const int ra = s - 5;
+    if (FULL || (s - 5 >= a0 - 4 && s - 5 <= a1 + 3)) {
       float D[4], om[4];
-      smooth(R.SIX[ra & 3][u], R.SIX[(ra - 1) & 3][u], R.SIX[(ra + 1) & 3][u],
-             R.SIX[ra & 3][u - 1], R.SIX[ra & 3][u + 1], w, D);
+      smooth(R.SIX[sl.template m4<5>()][u], R.SIX[sl.template m4<6>()][u],
+             R.SIX[sl.template m4<4>()][u], R.SIX[sl.template m4<5>()][u - 1],
+             R.SIX[sl.template m4<5>()][u + 1], w, D);
       weights<BMODE>(D, k.beta, om);
-      const Sten q = sten_x(R.A[(ra - 1) & 15] + u, R.A[ra & 15] + u, R.A[(ra + 1) & 15] + u,
-                            R.A[(ra + 2) & 15] + u);
+      const Sten q = sten_x(sl.template a<6>(), sl.template a<5>(), sl.template a<4>(),
+                            sl.template a<3>());
       float x = 0.f;
 #pragma unroll
       for (int d = 0; d < 4; ++d) x = fmaf(om[d], interp(q, d), x);
-      R.X[ra & 15][u] = x;
+      *sl.template x<5>() = x;
     }
-    // ---- "+" indicators, row s-7 ----
-    if (s - 7 >= a0 - 3 && s - 7 <= a1 + 2) {
-      const int r = s - 7;
-      const Sten qe = sten_e(R.A[r & 15] + u, R.X[(r - 2) & 15][u], R.X[(r - 1) & 15][u],
-                             R.X[r & 15][u], R.X[(r + 1) & 15][u]);
-      R.SIE[r & 3][u] = indicators(qe, k.kappa2, k.eps2);
-      const Sten qs = sten_s(R.X[r & 15] + u, R.A[(r - 1) & 15][u], R.A[r & 15][u],
-                             R.A[(r + 1) & 15][u], R.A[(r + 2) & 15][u]);
-      R.SIS[r & 3][u] = indicators(qs, k.kappa2, k.eps2);
+    // ---- "+" indicators, row r = s-7 ----
+    if (FULL || (s - 7 >= a0 - 3 && s - 7 <= a1 + 2)) {
+      const Sten qe = sten_e(sl.template a<7>(), *sl.template x<9>(), *sl.template x<8>(),
+                             *sl.template x<7>(), *sl.template x<6>());
+      R.SIE[sl.template m4<7>()][u] = indicators(qe, k.kappa2, k.eps2);
+      const Sten qs = sten_s(sl.template x<7>(), *sl.template a<8>(), *sl.template a<7>(),
+                             *sl.template a<6>(), *sl.template a<5>());
+      R.SIS[sl.template m4<7>()][u] = indicators(qs, k.kappa2, k.eps2);
     }
-    // ---- "+" adjoints, row s-9 ----
+    // ---- "+" adjoints, row r = s-9 ----
     float4 pe0 = make_float4(0.f, 0.f, 0.f, 0.f), ps0 = pe0;
-    if (s - 9 >= a0 - 2 && s - 9 <= a1 + 1) {
-      const int r = s - 9;
+    if (FULL || (s - 9 >= a0 - 2 && s - 9 <= a1 + 1)) {
       float4 de = pe0, ds = pe0;
-      if (ue_s != 0.f) {
+      if (FULL || ue_s != 0.f) {
         // E(r,c): D reads S at (r-1,c), (r,c), (r-1,c+1), (r,c+1)
         float D[4];
-        smooth(R.SIE[r & 3][u], R.SIS[(r - 1) & 3][u], R.SIS[r & 3][u],
-               R.SIS[(r - 1) & 3][u + 1], R.SIS[r & 3][u + 1], w, D);
-        const Sten q = sten_e(R.A[r & 15] + u, R.X[(r - 2) & 15][u], R.X[(r - 1) & 15][u],
-                              R.X[r & 15][u], R.X[(r + 1) & 15][u]);
+        smooth(R.SIE[sl.template m4<9>()][u], R.SIS[sl.template m4<10>()][u],
+               R.SIS[sl.template m4<9>()][u], R.SIS[sl.template m4<10>()][u + 1],
+               R.SIS[sl.template m4<9>()][u + 1], w, D);
+        const Sten q = sten_e(sl.template a<9>(), *sl.template x<11>(), *sl.template x<10>(),
+                              *sl.template x<9>(), *sl.template x<8>());
         point_adjoint<BMODE>(q, D, k.beta, ue_s, pe0, de);
       }
-      if (us_s != 0.f) {
+      if (FULL || us_s != 0.f) {
         // S(r,c): D reads E at (r,c-1), (r,c), (r+1,c-1), (r+1,c)
         float D[4];
-        smooth(R.SIS[r & 3][u], R.SIE[r & 3][u - 1], R.SIE[r & 3][u],
-               R.SIE[(r + 1) & 3][u - 1], R.SIE[(r + 1) & 3][u], w, D);
-        const Sten q = sten_s(R.X[r & 15] + u, R.A[(r - 1) & 15][u], R.A[r & 15][u],
-                              R.A[(r + 1) & 15][u], R.A[(r + 2) & 15][u]);
+        smooth(R.SIS[sl.template m4<9>()][u], R.SIE[sl.template m4<9>()][u - 1],
+               R.SIE[sl.template m4<9>()][u], R.SIE[sl.template m4<8>()][u - 1],
+               R.SIE[sl.template m4<8>()][u], w, D);
+        const Sten q = sten_s(sl.template x<9>(), *sl.template a<10>(), *sl.template a<9>(),
+                              *sl.template a<8>(), *sl.template a<7>());
         point_adjoint<BMODE>(q, D, k.beta, us_s, ps0, ds);
       }
-      R.DE[r & 3][u] = de;
-      R.DS[r & 3][u] = ds;
+      R.DE[sl.template m4<9>()][u] = de;
+      R.DS[sl.template m4<9>()][u] = ds;
     }
     // ---- "+" coefficients, row r = s-11 ----
-    {
-      const int r = s - 11;
-      const bool live = r >= a0 - 2 && r <= a1 + 1;
+    if (FULL || (s - 11 >= a0 - 2 && s - 11 <= a1 + 1)) {
       // E(r,c) is read by S(r,c), S(r,c+1), S(r-1,c), S(r-1,c+1)
       float sb[4];
-      if (live) {
-        float eh[4] = {0.f, 0.f, 0.f, 0.f};
-        {
-          smooth(R.DE[r & 3][u], R.DS[r & 3][u], R.DS[r & 3][u + 1], R.DS[(r - 1) & 3][u],
-                 R.DS[(r - 1) & 3][u + 1], w, sb);
-          const float4 pb = pe2;
-          if ((pb.x != 0.f || pb.y != 0.f || pb.z != 0.f || pb.w != 0.f) ||
-              (sb[0] != 0.f || sb[1] != 0.f || sb[2] != 0.f || sb[3] != 0.f)) {
-            const Sten q = sten_e(R.A[r & 15] + u, R.X[(r - 2) & 15][u], R.X[(r - 1) & 15][u],
-                                  R.X[r & 15][u], R.X[(r + 1) & 15][u]);
-            float cf[4][3];
-            node_coefs(q, pb, sb, k2, cf);
-            // along row r (samples): targets columns c-1, c, c+1, c+2
-            eh[0] = cf[1][2];
-            eh[1] = cf[0][0] + cf[1][1];
-            eh[2] = cf[0][1] + cf[1][0];
-            eh[3] = cf[0][2];
-            // along column c (x values): rows r-2 .. r+1
-            xacc[0] += cf[3][2];
-            xacc[1] += cf[2][0] + cf[3][1];
-            xacc[2] += cf[2][1] + cf[3][0];
-            xacc[3] += cf[2][2];
-          }
-        }
-#pragma unroll
-        for (int j = 0; j < 4; ++j) R.EH[j][r & 1][u] = eh[j];
-        // S(r,c) is read by E(r,c), E(r+1,c), E(r,c-1), E(r+1,c-1)
-        float sh[4] = {0.f, 0.f, 0.f, 0.f};
-        {
-          smooth(R.DS[r & 3][u], R.DE[r & 3][u], R.DE[(r + 1) & 3][u], R.DE[r & 3][u - 1],
-                 R.DE[(r + 1) & 3][u - 1], w, sb);
-          const float4 pb = ps2;
-          if ((pb.x != 0.f || pb.y != 0.f || pb.z != 0.f || pb.w != 0.f) ||
-              (sb[0] != 0.f || sb[1] != 0.f || sb[2] != 0.f || sb[3] != 0.f)) {
-            const Sten q = sten_s(R.X[r & 15] + u, R.A[(r - 1) & 15][u], R.A[r & 15][u],
-                                  R.A[(r + 1) & 15][u], R.A[(r + 2) & 15][u]);
-            float cf[4][3];
-            node_coefs(q, pb, sb, k2, cf);
-            // along row r (x values): targets columns c-2, c-1, c, c+1
-            sh[0] = cf[1][2];
-            sh[1] = cf[0][0] + cf[1][1];
-            sh[2] = cf[0][1] + cf[1][0];
-            sh[3] = cf[0][2];
-            // along column c (samples): rows r-1 .. r+2
-            aacc[0] += cf[3][2];
-            aacc[1] += cf[2][0] + cf[3][1];
-            aacc[2] += cf[2][1] + cf[3][0];
-            aacc[3] += cf[2][2];
-          }
-        }
-#pragma unroll
-        for (int j = 0; j < 4; ++j) R.SH[j][r & 3][u] = sh[j];
+      float eh[4] = {0.f, 0.f, 0.f, 0.f};
+      smooth(R.DE[sl.template m4<11>()][u], R.DS[sl.template m4<11>()][u],
+             R.DS[sl.template m4<11>()][u + 1], R.DS[sl.template m4<12>()][u],
+             R.DS[sl.template m4<12>()][u + 1], w, sb);
+      if (FULL || any_nonzero(pe2, sb)) {
+        const Sten q = sten_e(sl.template a<11>(), *sl.template x<13>(), *sl.template x<12>(),
+                              *sl.template x<11>(), *sl.template x<10>());
+        float cf[4][3];
+        node_coefs(q, pe2, sb, k2, cf);
+        // along row r (samples): targets columns c-1, c, c+1, c+2
+        eh[0] = cf[1][2];
+        eh[1] = cf[0][0] + cf[1][1];
+        eh[2] = cf[0][1] + cf[1][0];
+        eh[3] = cf[0][2];
+        // along column c (x values): rows r-2 .. r+1
+        xacc[0] += cf[3][2];
+        xacc[1] += cf[2][0] + cf[3][1];
+        xacc[2] += cf[2][1] + cf[3][0];
+        xacc[3] += cf[2][2];
       }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) R.EH[j][sl.template m2<11>()][u] = eh[j];
+      // S(r,c) is read by E(r,c), E(r+1,c), E(r,c-1), E(r+1,c-1)
+      float sh[4] = {0.f, 0.f, 0.f, 0.f};
+      smooth(R.DS[sl.template m4<11>()][u], R.DE[sl.template m4<11>()][u],
+             R.DE[sl.template m4<10>()][u], R.DE[sl.template m4<11>()][u - 1],
+             R.DE[sl.template m4<10>()][u - 1], w, sb);
+      if (FULL || any_nonzero(ps2, sb)) {
+        const Sten q = sten_s(sl.template x<11>(), *sl.template a<12>(), *sl.template a<11>(),
+                              *sl.template a<10>(), *sl.template a<9>());
+        float cf[4][3];
+        node_coefs(q, ps2, sb, k2, cf);
+        // along row r (x values): targets columns c-2, c-1, c, c+1
+        sh[0] = cf[1][2];
+        sh[1] = cf[0][0] + cf[1][1];
+        sh[2] = cf[0][1] + cf[1][0];
+        sh[3] = cf[0][2];
+        // along column c (samples): rows r-1 .. r+2
+        aacc[0] += cf[3][2];
+        aacc[1] += cf[2][0] + cf[3][1];
+        aacc[2] += cf[2][1] + cf[3][0];
+        aacc[3] += cf[2][2];
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) R.SH[j][sl.template m4<11>()][u] = sh[j];
+    }
 
-      // ---- X_bar of row r-2 and the partial A_bar of row r-1 are complete ----
-      const int q = r - 2, p = r - 1;
-      const float xb = xacc[0] + (R.SH[0][q & 3][u + 2] + R.SH[1][q & 3][u + 1]) +
-                       (R.SH[2][q & 3][u] + R.SH[3][q & 3][u - 1]) + gx_s;
-      const float ab = aacc[0] + (R.EH[0][p & 1][u + 1] + R.EH[1][p & 1][u]) +
-                       (R.EH[2][p & 1][u - 1] + R.EH[3][p & 1][u - 2]) + ga_s;
-      if (col_out && q >= a0 && q < a1) ws.xb[ws.idx(q, c)] = xb;
-      if (col_out && p >= a0 && p < a1) ws.ab[ws.idx(p, c)] = ab;
+    // ---- X_bar of row q = s-13 and the partial A_bar of row p = s-12 are complete ----
+    {
+      const int q = s - 13, p = s - 12;
+      const int sq = sl.template m4<13>(), sp = sl.template m2<12>();
+      const float xb = xacc[0] + (R.SH[0][sq][u + 2] + R.SH[1][sq][u + 1]) +
+                       (R.SH[2][sq][u] + R.SH[3][sq][u - 1]) + gx_s;
+      const float ab = aacc[0] + (R.EH[0][sp][u + 1] + R.EH[1][sp][u]) +
+                       (R.EH[2][sp][u - 1] + R.EH[3][sp][u - 2]) + ga_s;
+      if (col_out && (FULL || (q >= a0 && q < a1))) ws.xb[ws.idx(q, c)] = xb;
+      if (col_out && (FULL || (p >= a0 && p < a1))) ws.ab[ws.idx(p, c)] = ab;
       xacc[0] = xacc[1]; xacc[1] = xacc[2]; xacc[2] = xacc[3]; xacc[3] = 0.f;
       aacc[0] = aacc[1]; aacc[1] = aacc[2]; aacc[2] = aacc[3]; aacc[3] = 0.f;
     }
     pe2 = pe1; pe1 = pe0;
     ps2 = ps1; ps1 = ps0;
   }
+};
+
+template <int BMODE, int NT1>
+__global__ void __launch_bounds__(NT1, NT1 == NT_NARROW ? 3 : 2)
+    k_bwd_plus(BwdArgs a, MethodConsts k, int rows) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  RingsPlus<NT1>& R = *reinterpret_cast<RingsPlus<NT1>*>(smem);
+  {
+    float* z = reinterpret_cast<float*>(smem);
+    for (int i = threadIdx.x; i < (int)(sizeof(RingsPlus<NT1>) / sizeof(float)); i += NT1)
+      z[i] = 0.f;
+  }
+  PlusSweep<BMODE, NT1> sw(R, a, k, rows);
+  const int s_begin = sw.a0 - 6, s_end = sw.a1 - 1 + 13;
+  const int n = sw.n;
+  sw.pf = __ldg(sw.xin + (int64_t)clampi(s_begin, 0, n - 1) * sw.x_sh);
+  sw.pf2 = __ldg(sw.xin + (int64_t)clampi(s_begin + 1, 0, n - 1) * sw.x_sh);
+  sw.ue = sw.godd.template at<false>(2 * (s_begin - 9));
+  sw.us = sw.gevn.template at<false>(2 * (s_begin - 9) + 1);
+  sw.gx = sw.godd.template at<false>(2 * (s_begin - 13) + 1);
+  sw.ga = sw.gevn.template at<false>(2 * (s_begin - 12));
+  sw.pe1 = sw.pe2 = sw.ps1 = sw.ps2 = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) sw.xacc[j] = sw.aacc[j] = 0.f;
+  // FULL steps: every stage live and every output row written (s in
+  // [a0 + 13, a1 + 7]), and the output-gradient rows a step loads inside
+  // the output (2 (s - 12) + 1 >= 0, 2 (s - 8) + 1 < orows)
+  const int s_lo = max(sw.a0 + 13, 12);
+  const int s_hi = min(sw.a1 + 7, (sw.gevn.orows - 2) / 2 + 8);
+  sweep_band(sw, &R.A[0][sw.u], &R.X[0][sw.u], s_begin, s_end, s_lo, s_hi);
 }
 
 // ---- k_bwd_cross ---------------------------------------------------------------
 // Lags: input row 0, x indicators 3, x adjoints 5, x coefficients 7; A_bar
 // of row s - 9 is complete at step s and written (column-folded) at s + 1.
 template <int BMODE, int NT2>
-__global__ void __launch_bounds__(NT2, 3) k_bwd_cross(BwdArgs a, MethodConsts k, int rows) {
-  constexpr int TW2 = NT2 - HL2 - HR2;
-  extern __shared__ __align__(16) unsigned char smem[];
-  RingsCross<NT2>& R = *reinterpret_cast<RingsCross<NT2>*>(smem);
-  const int t = threadIdx.x;
-  const int64_t plane = blockIdx.z;
-  const int n = (int)a.n, m = (int)a.m;
-  const int nby = (int)gridDim.y;
-  const int b0 = (int)blockIdx.x * TW2;
-  const int b1 = min(b0 + TW2, m);
-  const int c = b0 - HL2 + t;
-  // A_bar rows of this band: image rows [r0, r1) plus the ghost rows that
-  // fold onto row 0 (first band) and row n-1 (last band)
-  const int r0 = (int)blockIdx.y * rows, r1 = min(r0 + rows, n);
-  const int a0 = blockIdx.y == 0 ? -GA : r0;
-  const int a1 = (int)blockIdx.y == nby - 1 ? n + GA : r1;
-  const float* xin = a.x + plane * a.x_sc + (int64_t)clampi(c, 0, m - 1) * a.x_sw;
-  const WsPlane ws = ws_plane(a, plane);
-  const bool cg = c >= -BWD_GHOST && c < m + BWD_GHOST;  // column on the workspace grid
+struct CrossSweep {
+  static constexpr int W = RingsCross<NT2>::W;
+  RingsCross<NT2>& R;
+  const MethodConsts k;
+  float w, k1;
+  int u, c, n, a0, a1;
+  const float* xin;
+  int64_t x_sh;
+  WsPlane ws;
+  bool cg;  // column on the workspace grid
   // the thread writes grad_in column c; columns 0 and m-1 also sum the ghost
   // columns folded onto them
-  const bool emit_col = c >= b0 && c < b1;
-  const bool fold_left = c == 0, fold_right = c == m - 1;
-  const float w = k.w;
-  const float k1 = k.kappa1 * k.kappa1;
+  bool emit_col, fold_left, fold_right;
+  float* gin;  // grad_in column c, row 0
+  int64_t gi_sh;
+  // carried from step to step
+  float pf, pf2;    // input rows s+1, s+2 of the column
+  float xbn, abn;   // workspace values of the next step's rows
+  float acc[4];     // A_bar rows s-9 .. s-6 of this column
+  float rowsum;     // ghost rows folded onto an edge row
+  int emitted;      // grad_in row published in the previous step (-1: none)
 
-  {
-    float* z = reinterpret_cast<float*>(smem);
-    for (int i = t; i < (int)(sizeof(RingsCross<NT2>) / sizeof(float)); i += NT2) z[i] = 0.f;
+  __device__ __forceinline__ CrossSweep(RingsCross<NT2>& R_, const BwdArgs& a,
+                                        const MethodConsts& k_, int rows)
+      : R(R_), k(k_) {
+    constexpr int TW2 = NT2 - HL2 - HR2;
+    const int t = threadIdx.x;
+    const int64_t plane = blockIdx.z;
+    n = (int)a.n;
+    const int m = (int)a.m;
+    const int nby = (int)gridDim.y;
+    const int b0 = (int)blockIdx.x * TW2;
+    const int b1 = min(b0 + TW2, m);
+    c = b0 - HL2 + t;
+    // A_bar rows of this band: image rows [r0, r1) plus the ghost rows that
+    // fold onto row 0 (first band) and row n-1 (last band)
+    const int r0 = (int)blockIdx.y * rows, r1 = min(r0 + rows, n);
+    a0 = blockIdx.y == 0 ? -GA : r0;
+    a1 = (int)blockIdx.y == nby - 1 ? n + GA : r1;
+    xin = a.x + plane * a.x_sc + (int64_t)clampi(c, 0, m - 1) * a.x_sw;
+    x_sh = a.x_sh;
+    ws = ws_plane(a, plane);
+    cg = c >= -BWD_GHOST && c < m + BWD_GHOST;
+    emit_col = c >= b0 && c < b1;
+    fold_left = c == 0;
+    fold_right = c == m - 1;
+    gin = a.gin + plane * a.gi_sc + (int64_t)(emit_col ? c : 0) * a.gi_sw;
+    gi_sh = a.gi_sh;
+    w = k.w;
+    k1 = k.kappa1 * k.kappa1;
+    u = t + PAD;
   }
-  const int u = t + PAD;
-  const int s_begin = a0 - 5, s_end = a1 - 1 + 10;
-  float pf = __ldg(xin + (int64_t)clampi(s_begin, 0, n - 1) * a.x_sh);
-  float pf2 = __ldg(xin + (int64_t)clampi(s_begin + 1, 0, n - 1) * a.x_sh);
-  // workspace values of the next step's rows, loaded one step ahead
-  auto ws_at = [&](const float* base, int r) -> float {
-    return (cg && r >= -BWD_GHOST && r < n + BWD_GHOST) ? base[ws.idx(r, c)] : 0.f;
-  };
-  float xbn = ws_at(ws.xb, s_begin - 5), abn = ws_at(ws.ab, s_begin - 9);
-  float acc[4] = {0.f, 0.f, 0.f, 0.f};  // A_bar rows s-9 .. s-6 of this column
-  float rowsum = 0.f;                    // ghost rows folded onto an edge row
-  int emitted = -1;                      // grad_in row published in the previous step
 
-  for (int s = s_begin; s <= s_end; ++s) {
+  // FULL steps read workspace rows known to lie on the workspace grid
+  template <bool FULL>
+  __device__ __forceinline__ float ws_at(const float* base, int r) const {
+    if (FULL) return cg ? base[ws.idx(r, c)] : 0.f;
+    return (cg && r >= -BWD_GHOST && r < n + BWD_GHOST) ? base[ws.idx(r, c)] : 0.f;
+  }
+
+  template <bool FULL, class SL>
+  __device__ __forceinline__ void step(const int s, const SL& sl) {
     const float cur = pf;
     pf = pf2;
-    pf2 = __ldg(xin + (int64_t)clampi(s + 2, 0, n - 1) * a.x_sh);
+    pf2 = __ldg(xin + (int64_t)clampi(s + 2, 0, n - 1) * x_sh);
     const float xb_s = xbn, ab_s = abn;
-    xbn = ws_at(ws.xb, s - 4);
-    abn = ws_at(ws.ab, s - 8);
+    xbn = ws_at<FULL>(ws.xb, s - 4);
+    abn = ws_at<FULL>(ws.ab, s - 8);
     __syncthreads();
-    R.A[s & 15][u] = cur;
+    *sl.template a<0>() = cur;
 
     // ---- grad_in row published in the previous step: fold the ghost columns ----
-    if (emitted >= 0 && emit_col) {
-      const float* af = R.AF[(s - 1) & 1] + u;
+    if ((FULL || emitted >= 0) && emit_col) {
+      const float* af = R.AF[sl.template m2<1>()] + u;
       float v = af[0];
       if (fold_left) v += (af[-5] + af[-4]) + (af[-3] + af[-2]) + af[-1];
       if (fold_right) v += (af[1] + af[2]) + (af[3] + af[4]) + af[5];
-      a.gin[plane * a.gi_sc + (int64_t)emitted * a.gi_sh + (int64_t)c * a.gi_sw] = v;
+      gin[(int64_t)(FULL ? s - 10 : emitted) * gi_sh] = v;
     }
 
     // Stages run only on the rows the band's outputs need (uniform guards).
     // ---- x indicators, row s-3 ----
-    if (s - 3 >= a0 - 4 && s - 3 <= a1 + 2) {
-      const int ra = s - 3;
-      const Sten q = sten_x(R.A[(ra - 1) & 15] + u, R.A[ra & 15] + u, R.A[(ra + 1) & 15] + u,
-                            R.A[(ra + 2) & 15] + u);
-      R.SIX[ra & 3][u] = indicators(q, k.kappa1, k.eps1);
+    if (FULL || (s - 3 >= a0 - 4 && s - 3 <= a1 + 2)) {
+      const Sten q = sten_x(sl.template a<4>(), sl.template a<3>(), sl.template a<2>(),
+                            sl.template a<1>());
+      R.SIX[sl.template m4<3>()][u] = indicators(q, k.kappa1, k.eps1);
     }
     // ---- x adjoints, row s-5 ----
-    if (s - 5 >= a0 - 3 && s - 5 <= a1 + 1) {
-      const int ra = s - 5;
-      const float xb = xb_s;
+    if (FULL || (s - 5 >= a0 - 3 && s - 5 <= a1 + 1)) {
       float4 px = make_float4(0.f, 0.f, 0.f, 0.f), dx = px;
-      if (xb != 0.f) {
+      if (FULL || xb_s != 0.f) {
         float D[4];
-        smooth(R.SIX[ra & 3][u], R.SIX[(ra - 1) & 3][u], R.SIX[(ra + 1) & 3][u],
-               R.SIX[ra & 3][u - 1], R.SIX[ra & 3][u + 1], w, D);
-        const Sten q = sten_x(R.A[(ra - 1) & 15] + u, R.A[ra & 15] + u,
-                              R.A[(ra + 1) & 15] + u, R.A[(ra + 2) & 15] + u);
-        point_adjoint<BMODE>(q, D, k.beta, xb, px, dx);
+        smooth(R.SIX[sl.template m4<5>()][u], R.SIX[sl.template m4<6>()][u],
+               R.SIX[sl.template m4<4>()][u], R.SIX[sl.template m4<5>()][u - 1],
+               R.SIX[sl.template m4<5>()][u + 1], w, D);
+        const Sten q = sten_x(sl.template a<6>(), sl.template a<5>(), sl.template a<4>(),
+                              sl.template a<3>());
+        point_adjoint<BMODE>(q, D, k.beta, xb_s, px, dx);
       }
-      R.PX[ra & 3][u] = px;
-      R.DX[ra & 3][u] = dx;
+      R.PX[sl.template m4<5>()][u] = px;
+      R.DX[sl.template m4<5>()][u] = dx;
     }
     // ---- x coefficients, row s-7 ----
-    if (s - 7 >= a0 - 2 && s - 7 <= a1) {
-      const int ra = s - 7;
+    if (FULL || (s - 7 >= a0 - 2 && s - 7 <= a1)) {
       float sb[4];
-      smooth(R.DX[ra & 3][u], R.DX[(ra - 1) & 3][u], R.DX[(ra + 1) & 3][u],
-             R.DX[ra & 3][u - 1], R.DX[ra & 3][u + 1], w, sb);
-      const float4 pb = R.PX[ra & 3][u];
+      smooth(R.DX[sl.template m4<7>()][u], R.DX[sl.template m4<8>()][u],
+             R.DX[sl.template m4<6>()][u], R.DX[sl.template m4<7>()][u - 1],
+             R.DX[sl.template m4<7>()][u + 1], w, sb);
+      const float4 pb = R.PX[sl.template m4<7>()][u];
       float2 c1 = make_float2(0.f, 0.f), c2 = c1, cm = c1;
-      if ((pb.x != 0.f || pb.y != 0.f || pb.z != 0.f || pb.w != 0.f) ||
-          (sb[0] != 0.f || sb[1] != 0.f || sb[2] != 0.f || sb[3] != 0.f)) {
-        const Sten q = sten_x(R.A[(ra - 1) & 15] + u, R.A[ra & 15] + u,
-                              R.A[(ra + 1) & 15] + u, R.A[(ra + 2) & 15] + u);
+      if (FULL || any_nonzero(pb, sb)) {
+        const Sten q = sten_x(sl.template a<8>(), sl.template a<7>(), sl.template a<6>(),
+                              sl.template a<5>());
         float cf[4][3];
         node_coefs(q, pb, sb, k1, cf);
         // targets (row offset, column offset): (0,0) d0.N0 + d1.N1,
         // (1,1) d0.N1 + d1.N0, (2,2) d0.N2, (-1,-1) d1.N2, (0,1) d2.N0 + d3.N1,
         // (1,0) d2.N1 + d3.N0, (2,-1) d2.N2, (-1,2) d3.N2
-        acc[2] += cf[0][0] + cf[1][1];  // row ra   (= s-7)
-        acc[3] += cf[2][1] + cf[3][0];  // row ra+1
+        acc[2] += cf[0][0] + cf[1][1];  // row s-7
+        acc[3] += cf[2][1] + cf[3][0];  // row s-6
         c1 = make_float2(cf[2][0] + cf[3][1], cf[0][1] + cf[1][0]);
         c2 = make_float2(cf[0][2], cf[3][2]);
         cm = make_float2(cf[1][2], cf[2][2]);
       }
-      R.C1[ra & 1][u] = c1;
-      R.C2[ra & 1][u] = c2;
-      R.CM[ra & 1][u] = cm;
+      R.C1[sl.template m2<7>()][u] = c1;
+      R.C2[sl.template m2<7>()][u] = c2;
+      R.CM[sl.template m2<7>()][u] = cm;
     }
     // ---- contributions of x row s-8 from the neighbouring columns ----
-    if (s - 8 >= a0 - 2 && s - 8 <= a1) {
-      const int rp = s - 8;
-      const float2 c1 = R.C1[rp & 1][u - 1];  // from column c-1: rows rp, rp+1
-      const float2 c2 = R.C2[rp & 1][u - 2];  // from column c-2: rows rp+2, rp-1
-      const float2 cm = R.CM[rp & 1][u + 1];  // from column c+1: rows rp-1, rp+2
+    if (FULL || (s - 8 >= a0 - 2 && s - 8 <= a1)) {
+      const int sp = sl.template m2<8>();
+      const float2 c1 = R.C1[sp][u - 1];  // from column c-1: rows s-8, s-7
+      const float2 c2 = R.C2[sp][u - 2];  // from column c-2: rows s-6, s-9
+      const float2 cm = R.CM[sp][u + 1];  // from column c+1: rows s-9, s-6
       acc[0] += c2.y + cm.x;
       acc[1] += c1.x;
       acc[2] += c1.y;
       acc[3] += c2.x + cm.y;
     }
-    // ---- A_bar of row s-9 is complete ----
+    // ---- A_bar of row q = s-9 is complete ----
     {
       const int q = s - 9;
       const float ab = acc[0] + ab_s;
       acc[0] = acc[1]; acc[1] = acc[2]; acc[2] = acc[3]; acc[3] = 0.f;
-      emitted = -1;
-      if (q >= a0 && q < a1) {
-        rowsum += ab;
-        // rows -GA..0 fold onto row 0, rows n-1..n+GA-1 onto row n-1
-        if (q >= 0 && (q < n - 1 || q == n - 1 + GA)) {
-          emitted = min(q, n - 1);
-          R.AF[s & 1][u] = rowsum;
-          rowsum = 0.f;
+      if (FULL) {
+        // an interior row: no ghost rows to fold (rowsum is 0 here)
+        R.AF[sl.template m2<0>()][u] = ab;
+        emitted = q;
+      } else {
+        emitted = -1;
+        if (q >= a0 && q < a1) {
+          rowsum += ab;
+          // rows -GA..0 fold onto row 0, rows n-1..n+GA-1 onto row n-1
+          if (q >= 0 && (q < n - 1 || q == n - 1 + GA)) {
+            emitted = min(q, n - 1);
+            R.AF[sl.template m2<0>()][u] = rowsum;
+            rowsum = 0.f;
+          }
         }
       }
     }
   }
+};
+
+template <int BMODE, int NT2>
+__global__ void __launch_bounds__(NT2, 3) k_bwd_cross(BwdArgs a, MethodConsts k, int rows) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  RingsCross<NT2>& R = *reinterpret_cast<RingsCross<NT2>*>(smem);
+  {
+    float* z = reinterpret_cast<float*>(smem);
+    for (int i = threadIdx.x; i < (int)(sizeof(RingsCross<NT2>) / sizeof(float)); i += NT2)
+      z[i] = 0.f;
+  }
+  CrossSweep<BMODE, NT2> sw(R, a, k, rows);
+  const int s_begin = sw.a0 - 5, s_end = sw.a1 - 1 + 10;
+  const int n = sw.n;
+  sw.pf = __ldg(sw.xin + (int64_t)clampi(s_begin, 0, n - 1) * sw.x_sh);
+  sw.pf2 = __ldg(sw.xin + (int64_t)clampi(s_begin + 1, 0, n - 1) * sw.x_sh);
+  sw.xbn = sw.template ws_at<false>(sw.ws.xb, s_begin - 5);
+  sw.abn = sw.template ws_at<false>(sw.ws.ab, s_begin - 9);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) sw.acc[j] = 0.f;
+  sw.rowsum = 0.f;
+  sw.emitted = -1;
+  // FULL steps: every stage live (s in [a0 + 9, a1 + 5]), the previous and
+  // the current A_bar rows interior ones (s - 10 >= max(a0, 0),
+  // s - 9 < min(a1, n - 1)) and the workspace rows a step loads on the
+  // workspace grid (s - 4 < n + 2)
+  const int s_lo = max(sw.a0, 0) + 10;
+  const int s_hi = min(sw.a1, sw.n) + 5;
+  sweep_band(sw, &R.A[0][sw.u], &R.A[0][sw.u], s_begin, s_end, s_lo, s_hi);
 }
 
 // Rows per band: the band count that minimises waves x (rows + fill steps).
