@@ -382,6 +382,7 @@ struct PlusSweep {
   float pf, pf2;              // input rows s+1, s+2 of the column
   float ue, us, gx, ga;       // output gradients of the next step's rows
   float ue2, us2, gx2, ga2;   // and of the step after
+  float ue3, us3, gx3, ga3;   // and of the one after that
   float4 pe1, pe2, ps1, ps2;  // p_bar of the "+" points of rows s-10 (1), s-11 (2)
   float xacc[4], aacc[4];     // own-column accumulators: X_bar rows r-2 .. r+1,
                               // A_bar rows r-1 .. r+2 (r = the coefficient row)
@@ -417,10 +418,11 @@ struct PlusSweep {
     pf2 = __ldg(xin + (int64_t)clampi(s + 2, 0, n - 1) * x_sh);
     const float ue_s = ue, us_s = us, gx_s = gx, ga_s = ga;
     ue = ue2; us = us2; gx = gx2; ga = ga2;
-    ue2 = godd.template at<FULL>(2 * (s - 7));
-    us2 = gevn.template at<FULL>(2 * (s - 7) + 1);
-    gx2 = godd.template at<FULL>(2 * (s - 11) + 1);
-    ga2 = gevn.template at<FULL>(2 * (s - 10));
+    ue2 = ue3; us2 = us3; gx2 = gx3; ga2 = ga3;
+    ue3 = godd.template at<FULL>(2 * (s - 6));
+    us3 = gevn.template at<FULL>(2 * (s - 6) + 1);
+    gx3 = godd.template at<FULL>(2 * (s - 10) + 1);
+    ga3 = gevn.template at<FULL>(2 * (s - 9));
     __syncthreads();
     *sl.template a<0>() = cur;
 
@@ -575,14 +577,18 @@ __global__ void __launch_bounds__(NT1, NT1 == NT_NARROW ? 3 : 2)
   sw.us2 = sw.gevn.template at<false>(2 * (s_begin - 8) + 1);
   sw.gx2 = sw.godd.template at<false>(2 * (s_begin - 12) + 1);
   sw.ga2 = sw.gevn.template at<false>(2 * (s_begin - 11));
+  sw.ue3 = sw.godd.template at<false>(2 * (s_begin - 7));
+  sw.us3 = sw.gevn.template at<false>(2 * (s_begin - 7) + 1);
+  sw.gx3 = sw.godd.template at<false>(2 * (s_begin - 11) + 1);
+  sw.ga3 = sw.gevn.template at<false>(2 * (s_begin - 10));
   sw.pe1 = sw.pe2 = sw.ps1 = sw.ps2 = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
   for (int j = 0; j < 4; ++j) sw.xacc[j] = sw.aacc[j] = 0.f;
   // FULL steps: every stage live and every output row written (s in
   // [a0 + 13, a1 + 7]), and the output-gradient rows a step loads inside
-  // the output (2 (s - 11) + 1 >= 0, 2 (s - 7) + 1 < orows)
-  const int s_lo = max(sw.a0 + 13, 11);
-  const int s_hi = min(sw.a1 + 7, sw.gevn.orows >= 2 ? (sw.gevn.orows - 2) / 2 + 7 : 6);
+  // the output (2 (s - 10) + 1 >= 0, 2 (s - 6) + 1 < orows)
+  const int s_lo = max(sw.a0 + 13, 10);
+  const int s_hi = min(sw.a1 + 7, sw.gevn.orows >= 2 ? (sw.gevn.orows - 2) / 2 + 6 : 5);
   sweep_band(sw, &R.A[0][sw.u], &R.X[0][sw.u], s_begin, s_end, s_lo, s_hi);
 }
 
@@ -609,6 +615,7 @@ struct CrossSweep {
   float pf, pf2;    // input rows s+1, s+2 of the column
   float xbn, abn;   // workspace values of the next step's rows
   float xbn2, abn2; // and of the step after
+  float xbn3, abn3; // and of the one after that
   float acc[4];     // A_bar rows s-9 .. s-6 of this column
   float rowsum;     // ghost rows folded onto an edge row
   int emitted;      // grad_in row published in the previous step (-1: none)
@@ -659,8 +666,10 @@ struct CrossSweep {
     const float xb_s = xbn, ab_s = abn;
     xbn = xbn2;
     abn = abn2;
-    xbn2 = ws_at<FULL>(ws.xb, s - 3);
-    abn2 = ws_at<FULL>(ws.ab, s - 7);
+    xbn2 = xbn3;
+    abn2 = abn3;
+    xbn3 = ws_at<FULL>(ws.xb, s - 2);
+    abn3 = ws_at<FULL>(ws.ab, s - 6);
     __syncthreads();
     *sl.template a<0>() = cur;
 
@@ -775,6 +784,8 @@ __global__ void __launch_bounds__(NT2, 3) k_bwd_cross(BwdArgs a, MethodConsts k,
   sw.abn = sw.template ws_at<false>(sw.ws.ab, s_begin - 9);
   sw.xbn2 = sw.template ws_at<false>(sw.ws.xb, s_begin - 4);
   sw.abn2 = sw.template ws_at<false>(sw.ws.ab, s_begin - 8);
+  sw.xbn3 = sw.template ws_at<false>(sw.ws.xb, s_begin - 3);
+  sw.abn3 = sw.template ws_at<false>(sw.ws.ab, s_begin - 7);
 #pragma unroll
   for (int j = 0; j < 4; ++j) sw.acc[j] = 0.f;
   sw.rowsum = 0.f;
@@ -782,9 +793,9 @@ __global__ void __launch_bounds__(NT2, 3) k_bwd_cross(BwdArgs a, MethodConsts k,
   // FULL steps: every stage live (s in [a0 + 9, a1 + 5]), the previous and
   // the current A_bar rows interior ones (s - 10 >= max(a0, 0),
   // s - 9 < min(a1, n - 1)) and the workspace rows a step loads on the
-  // workspace grid (s - 3 < n + 2)
+  // workspace grid (s - 2 < n + 2)
   const int s_lo = max(sw.a0, 0) + 10;
-  const int s_hi = min(sw.a1 + 5, sw.n + 4);
+  const int s_hi = min(sw.a1 + 5, sw.n + 3);
   sweep_band(sw, &R.A[0][sw.u], &R.A[0][sw.u], s_begin, s_end, s_lo, s_hi);
 }
 
