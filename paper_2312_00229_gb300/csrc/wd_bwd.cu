@@ -61,8 +61,8 @@ struct RingsPlus {
   float4 SIX[4][W];   // phase-1 indicators (4 directions)
   float4 SIE[4][W];   // E-point indicators
   float4 SIS[4][W];   // S-point indicators
-  float4 DE[4][W];    // E D_bar
-  float4 DS[4][W];    // S D_bar
+  float4 DE[4][W];    // E 2 D_bar
+  float4 DS[4][W];    // S 2 D_bar
   // Row stencils' node contributions pre-summed by target column, one array
   // per target so that each gather reads a scalar per thread (no strided
   // component reads of a vector array)
@@ -76,7 +76,7 @@ struct RingsCross {
   float A[16][W];
   float4 SIX[4][W];
   float4 PX[4][W];    // x p_bar
-  float4 DX[4][W];    // x D_bar
+  float4 DX[4][W];    // x 2 D_bar
   float2 C1[2][W];    // contributions to column c+1: rows a, a+1
   float2 C2[2][W];    // to column c+2: rows a+2, a-1
   float2 CM[2][W];    // to column c-1: rows a-1, a+2
@@ -190,7 +190,8 @@ __device__ __forceinline__ float interp(const Sten& q, int k) {
   return fmaf(-0.125f, q.s[k], 0.5f * q.M[k >> 1]);
 }
 
-// p_bar, D_bar of one blend point given its D and stencil data.
+// p_bar and 2 D_bar of one blend point given its D and stencil data (D_bar
+// is carried doubled: the node coefficients' factors of 2 fold into it).
 template <int BMODE>
 __device__ __forceinline__ void point_adjoint(const Sten& q, const float D[4], float beta,
                                               float ub, float4& pb4, float4& db4) {
@@ -205,7 +206,7 @@ __device__ __forceinline__ void point_adjoint(const Sten& q, const float D[4], f
   const float d3 = fmaf(-0.125f, q.s[3] - q.s[0], hM);
   const float v = fmaf(om[1], d1, fmaf(om[2], d2, om[3] * d3));
   const float pu[4] = {-v, d1 - v, d2 - v, d3 - v};
-  const float ubb = -ub * beta;
+  const float ubb = -ub * (2.f * beta);
 #pragma unroll
   for (int kk = 0; kk < 4; ++kk) {
     pb[kk] = ub * om[kk];
@@ -215,13 +216,14 @@ __device__ __forceinline__ void point_adjoint(const Sten& q, const float D[4], f
   db4 = make_float4(db[0], db[1], db[2], db[3]);
 }
 
-// Node coefficients (N0, N1, N2) of the four stencils of a point.
-__device__ __forceinline__ void node_coefs(const Sten& q, const float4& pb, const float sb[4],
+// Node coefficients (N0, N1, N2) of the four stencils of a point; sb2 holds
+// 2 SI_bar.
+__device__ __forceinline__ void node_coefs(const Sten& q, const float4& pb, const float sb2[4],
                                            float k2, float c[4][3]) {
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    const float pbar = comp(pb, k), sbar = sb[k];
-    const float g2 = 2.f * q.g[k] * sbar, s2 = 2.f * k2 * q.s[k] * sbar;
+    const float pbar = comp(pb, k), sbar2 = sb2[k];
+    const float g2 = q.g[k] * sbar2, s2 = k2 * q.s[k] * sbar2;
     c[k][0] = fmaf(0.375f, pbar, s2 - g2);
     c[k][1] = fmaf(0.75f, pbar, fmaf(-2.f, s2, g2));
     c[k][2] = fmaf(-0.125f, pbar, s2);
@@ -488,7 +490,7 @@ struct PlusSweep {
     // ---- "+" coefficients, row r = s-11 ----
     if (FULL || (s - 11 >= a0 - 2 && s - 11 <= a1 + 1)) {
       // E(r,c) is read by S(r,c), S(r,c+1), S(r-1,c), S(r-1,c+1)
-      float sb[4];
+      float sb[4];  // 2 SI_bar
       float eh[4] = {0.f, 0.f, 0.f, 0.f};
       smooth(R.DE[sl.template m4<11>()][u], R.DS[sl.template m4<11>()][u],
              R.DS[sl.template m4<11>()][u + 1], R.DS[sl.template m4<12>()][u],
@@ -612,7 +614,7 @@ struct CrossSweep {
   float* gin;  // grad_in column c, row 0
   int64_t gi_sh;
   // carried from step to step
-  float pf, pf2;    // input rows s+1, s+2 of the column
+  float pf, pf2, pf3, pf4;  // input rows s .. s+3 of the column
   float xbn, abn;   // workspace values of the next step's rows
   float xbn2, abn2; // and of the step after
   float xbn3, abn3; // and of the one after that
@@ -662,7 +664,9 @@ struct CrossSweep {
   __device__ __forceinline__ void step(const int s, const SL& sl) {
     const float cur = pf;
     pf = pf2;
-    pf2 = __ldg(xin + (int64_t)clampi(s + 2, 0, n - 1) * x_sh);
+    pf2 = pf3;
+    pf3 = pf4;
+    pf4 = __ldg(xin + (int64_t)clampi(s + 4, 0, n - 1) * x_sh);
     const float xb_s = xbn, ab_s = abn;
     xbn = xbn2;
     abn = abn2;
@@ -706,7 +710,7 @@ struct CrossSweep {
     }
     // ---- x coefficients, row s-7 ----
     if (FULL || (s - 7 >= a0 - 2 && s - 7 <= a1)) {
-      float sb[4];
+      float sb[4];  // 2 SI_bar
       smooth(R.DX[sl.template m4<7>()][u], R.DX[sl.template m4<8>()][u],
              R.DX[sl.template m4<6>()][u], R.DX[sl.template m4<7>()][u - 1],
              R.DX[sl.template m4<7>()][u + 1], w, sb);
@@ -780,6 +784,8 @@ __global__ void __launch_bounds__(NT2, 3) k_bwd_cross(BwdArgs a, MethodConsts k,
   const int n = sw.n;
   sw.pf = __ldg(sw.xin + (int64_t)clampi(s_begin, 0, n - 1) * sw.x_sh);
   sw.pf2 = __ldg(sw.xin + (int64_t)clampi(s_begin + 1, 0, n - 1) * sw.x_sh);
+  sw.pf3 = __ldg(sw.xin + (int64_t)clampi(s_begin + 2, 0, n - 1) * sw.x_sh);
+  sw.pf4 = __ldg(sw.xin + (int64_t)clampi(s_begin + 3, 0, n - 1) * sw.x_sh);
   sw.xbn = sw.template ws_at<false>(sw.ws.xb, s_begin - 5);
   sw.abn = sw.template ws_at<false>(sw.ws.ab, s_begin - 9);
   sw.xbn2 = sw.template ws_at<false>(sw.ws.xb, s_begin - 4);
