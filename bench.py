@@ -381,6 +381,29 @@ def time_graph(torch, fn_list, reps, warm=3):
     return e0.elapsed_time(e1) / 1e3 / reps, g
 
 
+def fp32_probe(torch, sms):
+    """Measured FP32 operation rate: the library's calibration kernel, 4 CTAs
+    of 256 threads per SM, median of 5 launches timed with CUDA events."""
+    import ctypes
+    from paper_2312_00229_gb300 import binding as B
+    blocks, iters = 4 * sms, 8192
+    out = torch.empty(blocks * 256, dtype=torch.float32, device="cuda")
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    ptr = ctypes.c_void_p(out.data_ptr())
+    B.check("weno_fp32_probe", B.weno_fp32_probe(blocks, iters, ptr, st))
+    ts = []
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        B.check("weno_fp32_probe", B.weno_fp32_probe(blocks, iters, ptr, st))
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1) / 1e3)
+    t = sorted(ts)[len(ts) // 2]
+    return {"ops_per_s": B.weno_fp32_probe_ops(blocks, iters) / t, "ms": round(t * 1e3, 3),
+            "launch": f"{blocks} CTAs x 256 threads x {iters * 128} FFMA each"}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -436,6 +459,7 @@ def run_ours(args):
     value = replica_value(world, frames, OUT_PX, t)
     per_launch = t_local / frames
 
+    probe = fp32_probe(torch, sms)
     pxch = H * W * C
     achieved_ops = ALGO_FP32_OPS_PER_PXCH * pxch / per_launch
     achieved_gbs = ALGO_BYTES_PER_PXCH["u8"] * pxch / per_launch / 1e9
@@ -454,6 +478,11 @@ def run_ours(args):
                 "peak_kind": "nominal FP32-pipe peak (not measured): SMs x 128 lanes x "
                              "maximum SM clock",
                 "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_max_mhz:.0f} MHz",
+                "peak_measured_probe": {
+                    "value": round(probe["ops_per_s"] / 1e12, 3), "unit": "Top/s",
+                    "frac": round(achieved_ops / probe["ops_per_s"], 4),
+                    "kernel": "weno_fp32_probe: 16 independent FFMA chains per thread",
+                    "launch": probe["launch"], "ms": probe["ms"]},
                 "sm_mhz_median_timed": sm_med,
                 "frac_at_sampled_clock": (round(achieved_ops / (sms * FP32_LANES_PER_SM *
                                                                  sm_med * 1e6), 4)

@@ -271,6 +271,20 @@ int weno_zoom2x_batched_noalloc(int count, const weno_image* d_in, weno_dtype in
                                 const weno_image* d_out, weno_dtype out_t, const weno_params* p,
                                 int rows_per_tile, int tile_width, void* stream);
 
+/* Calibration of the FP32 pipe (measurement support, not part of the
+ * method): launches `blocks` CTAs of 256 threads, each thread running
+ * `iters` x 128 FP32 fused multiply-adds in 16 independent chains, and
+ * writes one float per thread to `out` (device buffer of >= blocks x 256
+ * floats, caller-owned).  Timing the launch on `stream` gives the measured
+ * FP32 operation rate beside the nominal one (SMs x 128 lanes x clock).
+ * Returns WENO_OK, WENO_EINVAL (blocks or iters < 1, null out) or
+ * WENO_ECUDA. */
+int weno_fp32_probe(int blocks, int iters, float* out, void* stream);
+
+/* FP32 operations (one per fused multiply-add) one weno_fp32_probe launch
+ * performs. */
+long long weno_fp32_probe_ops(int blocks, int iters);
+
 #ifdef __cplusplus
 }
 #endif

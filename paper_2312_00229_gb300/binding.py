@@ -32,6 +32,8 @@ EXPORTS = (
     "weno_zoom2x_cascade",
     "weno_zoom2x_cascade_workspace_bytes",
     "weno_wait_timeouts",
+    "weno_fp32_probe",
+    "weno_fp32_probe_ops",
 )
 WENO_NOALLOC_MAX_IMAGES = 4096
 WENO_CASCADE_MAX_LEVELS = 6
@@ -85,6 +87,8 @@ _SIGS = {
     "weno_zoom2x_cascade": ([_IMG, ctypes.c_int, _IMG, ctypes.c_int, ctypes.c_int, _PRM, _VP,
                              ctypes.c_size_t, _VP], ctypes.c_int),
     "weno_zoom2x_cascade_workspace_bytes": ([_IMG, ctypes.c_int, _PRM], ctypes.c_size_t),
+    "weno_fp32_probe": ([ctypes.c_int, ctypes.c_int, _VP, _VP], ctypes.c_int),
+    "weno_fp32_probe_ops": ([ctypes.c_int, ctypes.c_int], ctypes.c_longlong),
 }
 
 _lock = threading.Lock()
@@ -197,3 +201,11 @@ def weno_wait_timeouts(reset: bool = False) -> int:
     v = ctypes.c_uint(0)
     check("weno_wait_timeouts", load().weno_wait_timeouts(ctypes.byref(v), 1 if reset else 0))
     return int(v.value)
+
+
+def weno_fp32_probe(blocks, iters, out, stream) -> int:
+    return load().weno_fp32_probe(int(blocks), int(iters), out, stream)
+
+
+def weno_fp32_probe_ops(blocks, iters) -> int:
+    return int(load().weno_fp32_probe_ops(int(blocks), int(iters)))

@@ -20,7 +20,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libwdweno.so")
 SOURCES = ["wd_api.cu", "wd_fwd.cu", "wd_fwd_typed.cu", "wd_fwd_typed_b2r.cu", "wd_batched.cu",
            "wd_batched2.cu", "wd_bwd.cu",
-           "wd_resample.cu", "wd_noalloc.cu", "wd_cascade.cu"]
+           "wd_resample.cu", "wd_noalloc.cu", "wd_cascade.cu", "wd_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -200,3 +200,11 @@ def test_package_exports_resolve():
     import paper_2312_00229_gb300 as pkg
     for name in pkg.__all__:
         assert getattr(pkg, name) is not None, name
+
+
+def test_fp32_probe_rejects_bad_arguments_and_counts_ops():
+    assert B.weno_fp32_probe(0, 1, 0x100, None) == B.WENO_EINVAL
+    assert B.weno_fp32_probe(1, 0, 0x100, None) == B.WENO_EINVAL
+    assert B.weno_fp32_probe(1, 1, None, None) == B.WENO_EINVAL
+    # 256 threads x 8 rounds x 16 chains per iteration
+    assert B.weno_fp32_probe_ops(3, 5) == 3 * 256 * 5 * 8 * 16
