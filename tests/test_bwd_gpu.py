@@ -117,6 +117,16 @@ def test_bwd_several_strips_and_bands(shape):
     _check(A, G, api.Params())
 
 
+@pytest.mark.parametrize("n", [14, 27, 33, 45, 58])
+def test_bwd_band_step_forms(n):
+    """Heights whose bands start at different rows modulo 4, so that the
+    sweeps switch between their guarded steps and their four-step groups of
+    guard-free steps at every alignment, and bands too short for any group."""
+    A = RNG.random((3, n, 70))
+    G = RNG.normal(size=(3, 2 * n, 140))
+    _check(A, G, api.Params())
+
+
 def test_bwd_windowed_at_bench_size():
     """32x3x512x512 planes (the fwd+bwd workload) with grad_out nonzero only in
     a 24x24 window of one plane: the gradient is compared with the FP64
