@@ -131,11 +131,13 @@ def tune_fwd(x: torch.Tensor, params=None, out_dtype=None, layout: str = "chw",
 
 def tune_cascade(x: torch.Tensor, levels: int, params=None, out_dtype=None,
                  inter_dtype=torch.float32, layout: str = "chw",
-                 candidates: Iterable[int] = CANDIDATES, reps: int = 10) -> list:
+                 candidates: Iterable[int] = CANDIDATES, reps: int = 10,
+                 only_missing: bool = False) -> list:
     """Tunes the tile shape of every level of ``api.cascade_zoom(x, levels)``
     (each level is its own size class: its input shape and storage pair),
     running the chain on `x` to get each level's input.  Returns the
-    per-level timing dicts of ``tune_fwd``."""
+    per-level timing dicts of ``tune_fwd`` (an empty dict for a level that
+    `only_missing` left with its cached shape)."""
     import dataclasses
 
     from . import api
@@ -146,8 +148,11 @@ def tune_cascade(x: torch.Tensor, levels: int, params=None, out_dtype=None,
         last = lvl == levels - 1
         p = dataclasses.replace(params, h=params.h / (1 << lvl), data_bound=bounds[lvl])
         odt = (out_dtype or x.dtype) if last else inter_dtype
-        out.append(tune_fwd(cur, p, out_dtype=odt, layout=layout, candidates=candidates,
-                            reps=reps))
+        if only_missing and size_class(cur, odt, layout) in _load():
+            out.append({})
+        else:
+            out.append(tune_fwd(cur, p, out_dtype=odt, layout=layout, candidates=candidates,
+                                reps=reps))
         cur = api.zoom2x_fwd(cur, p, out_dtype=odt, layout=layout)
     return out
 

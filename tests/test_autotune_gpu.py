@@ -56,3 +56,7 @@ def test_tune_cascade_keeps_every_output_bit(fresh_cache):
     got = api.cascade_zoom(x, 3)
     torch.cuda.synchronize()
     assert torch.equal(got, want)
+    # with every level cached, only_missing times nothing and keeps the shapes
+    before = dict(autotune._load())
+    again = autotune.tune_cascade(x, 3, candidates=(0, 16), reps=1, only_missing=True)
+    assert again == [{}, {}, {}] and autotune._load() == before
