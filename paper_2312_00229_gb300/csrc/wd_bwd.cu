@@ -34,6 +34,10 @@
 // Scatters are gathers: a contribution to a thread's own column is added to
 // a short register ring of row accumulators, contributions to other columns
 // are published per row in shared memory and gathered one step later.
+// In the middle of a band the steps run in groups of four with every ring
+// slot a compile-time constant and no stage guards (sweep_band); the global
+// values a step needs are loaded three (input rows: two or four) steps
+// before it.
 #include "wd_bwd.h"
 
 namespace wdweno {
