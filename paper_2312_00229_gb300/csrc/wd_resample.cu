@@ -65,6 +65,63 @@ __device__ __forceinline__ float weno1d_at(float v0, float v1, float v2, float v
   return fmaf(h, mix, fmaf(g, t, v1));
 }
 
+// Two interpolants at once on Blackwell's packed two-lane FP32 instructions
+// (fma / add / sub / mul .f32x2): weno1d_at on lane pairs, the same
+// expressions in the same order, each lane rounded as the scalar form.
+using f2 = float2;
+__device__ __forceinline__ f2 bc2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ f2 add2(f2 a, f2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) {
+  f2 r;
+  asm("{.reg .b64 ra, rb, rd;\n\t"
+      "mov.b64 ra, {%2, %3};\n\t"
+      "mov.b64 rb, {%4, %5};\n\t"
+      "sub.rn.f32x2 rd, ra, rb;\n\t"
+      "mov.b64 {%0, %1}, rd;}"
+      : "=f"(r.x), "=f"(r.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return r;
+}
+__device__ __forceinline__ f2 rcp2(f2 a) { return make_float2(rcp_approx(a.x), rcp_approx(a.y)); }
+
+template <int BMODE>
+__device__ __forceinline__ f2 weno1d_at2(f2 v0, f2 v1, f2 v2, f2 v3, f2 t, f2 C0, f2 h,
+                                         float eps, float beta) {
+  const f2 g = sub2(v2, v1);
+  const f2 sL = fma2(bc2(-2.f), v1, add2(v0, v2));
+  const f2 sR = fma2(bc2(-2.f), v2, add2(v1, v3));
+  const f2 C1 = sub2(bc2(1.f), C0);
+  f2 a0, a1;
+  if (BMODE == B0) {
+    a0 = C0; a1 = C1;
+  } else {
+    const f2 k2 = bc2(13.f / 12.f), e = bc2(eps);
+    const f2 eL = fma2(g, g, fma2(mul2(k2, sL), sL, e));
+    const f2 eR = fma2(g, g, fma2(mul2(k2, sR), sR, e));
+    if (BMODE == B2R) {
+      a0 = mul2(C0, mul2(eR, eR));
+      a1 = mul2(C1, mul2(eL, eL));
+    } else {
+      const f2 inv = rcp2(make_float2(fmaxf(eL.x, eR.x), fmaxf(eL.y, eR.y)));
+      const f2 rL = mul2(eL, inv), rR = mul2(eR, inv);
+      if (BMODE == B2) {
+        a0 = mul2(mul2(C0, rR), rR);
+        a1 = mul2(mul2(C1, rL), rL);
+      } else {
+        const f2 b = bc2(beta);
+        const f2 lR = mul2(b, make_float2(lg2_approx(rR.x), lg2_approx(rR.y)));
+        const f2 lL = mul2(b, make_float2(lg2_approx(rL.x), lg2_approx(rL.y)));
+        a0 = mul2(C0, make_float2(ex2_approx(lR.x), ex2_approx(lR.y)));
+        a1 = mul2(C1, make_float2(ex2_approx(lL.x), ex2_approx(lL.y)));
+      }
+    }
+  }
+  const f2 mix = mul2(fma2(a0, sL, mul2(a1, sR)), rcp2(add2(a0, a1)));
+  return fma2(h, mix, fma2(g, t, v1));
+}
+
 template <int BMODE>
 __device__ __forceinline__ float weno1d(float v0, float v1, float v2, float v3, float t,
                                         float eps, float beta) {
@@ -265,9 +322,19 @@ __global__ void __launch_bounds__(RS_THREADS) resample_tiled_kernel(ResampleArgs
     if (a.n > 1) {
       const float ty = row_t[r];
       const float C0 = (2.f - ty) * (1.f / 3.f), h = 0.5f * fmaf(ty, ty, -ty);
-      for (int k = lane; k < wc; k += 32)
-        z[r][k] = weno1d_at<BMODE>(w0[k], w0[k + RS_WC], w0[k + 2 * RS_WC], w0[k + 3 * RS_WC],
-                                   ty, C0, h, eps, beta);
+      // window columns k and k + 32 in the two lanes (a column past the
+      // window repeats k and is not stored)
+      for (int k = lane; k < wc; k += 64) {
+        const bool two = k + 32 < wc;
+        const int kb = two ? k + 32 : k;
+        const f2 zz = weno1d_at2<BMODE>(
+            make_float2(w0[k], w0[kb]), make_float2(w0[k + RS_WC], w0[kb + RS_WC]),
+            make_float2(w0[k + 2 * RS_WC], w0[kb + 2 * RS_WC]),
+            make_float2(w0[k + 3 * RS_WC], w0[kb + 3 * RS_WC]), bc2(ty), bc2(C0), bc2(h), eps,
+            beta);
+        z[r][k] = zz.x;
+        if (two) z[r][k + 32] = zz.y;
+      }
     } else {
       for (int k = lane; k < wc; k += 32) z[r][k] = w0[k + RS_WC];
     }
@@ -294,11 +361,22 @@ __global__ void __launch_bounds__(RS_THREADS) resample_tiled_kernel(ResampleArgs
   for (int r = warp; r < nr; r += RS_THREADS / 32, o += o_step) {
     float u[4];
     const float* zr = z[r];
+    // outputs q and q + 1 in the two lanes
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const float* zk = zr + kq[q];
-      u[q] = interp_x ? weno1d_at<BMODE>(zk[0], zk[1], zk[2], zk[3], tq[q], cq[q], hq[q], eps, beta)
-                      : zk[1];
+    for (int q = 0; q < 4; q += 2) {
+      const float* za = zr + kq[q];
+      const float* zb = zr + kq[q + 1];
+      if (interp_x) {
+        const f2 uu = weno1d_at2<BMODE>(
+            make_float2(za[0], zb[0]), make_float2(za[1], zb[1]), make_float2(za[2], zb[2]),
+            make_float2(za[3], zb[3]), make_float2(tq[q], tq[q + 1]),
+            make_float2(cq[q], cq[q + 1]), make_float2(hq[q], hq[q + 1]), eps, beta);
+        u[q] = uu.x;
+        u[q + 1] = uu.y;
+      } else {
+        u[q] = za[1];
+        u[q + 1] = zb[1];
+      }
     }
     if (a.out_vec4 && cn == 4) {
       rs_store4<TOut>(a.out, o, u, a.out_dtype, a.clamp_float);
