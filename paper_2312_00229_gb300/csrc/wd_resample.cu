@@ -17,6 +17,7 @@
 #include <type_traits>
 
 #include "wd_common.cuh"
+#include "wd_packed.cuh"
 #include "wd_resample.h"
 
 namespace wdweno {
@@ -66,60 +67,42 @@ __device__ __forceinline__ float weno1d_at(float v0, float v1, float v2, float v
 }
 
 // Two interpolants at once on Blackwell's packed two-lane FP32 instructions
-// (fma / add / sub / mul .f32x2): weno1d_at on lane pairs, the same
+// (pk_* helpers of wd_packed.cuh): weno1d_at on lane pairs, the same
 // expressions in the same order, each lane rounded as the scalar form.
-using f2 = float2;
-__device__ __forceinline__ f2 bc2(float v) { return make_float2(v, v); }
-__device__ __forceinline__ f2 add2(f2 a, f2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ f2 mul2(f2 a, f2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ f2 sub2(f2 a, f2 b) {
-  f2 r;
-  asm("{.reg .b64 ra, rb, rd;\n\t"
-      "mov.b64 ra, {%2, %3};\n\t"
-      "mov.b64 rb, {%4, %5};\n\t"
-      "sub.rn.f32x2 rd, ra, rb;\n\t"
-      "mov.b64 {%0, %1}, rd;}"
-      : "=f"(r.x), "=f"(r.y)
-      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
-  return r;
-}
-__device__ __forceinline__ f2 rcp2(f2 a) { return make_float2(rcp_approx(a.x), rcp_approx(a.y)); }
-
 template <int BMODE>
 __device__ __forceinline__ f2 weno1d_at2(f2 v0, f2 v1, f2 v2, f2 v3, f2 t, f2 C0, f2 h,
                                          float eps, float beta) {
-  const f2 g = sub2(v2, v1);
-  const f2 sL = fma2(bc2(-2.f), v1, add2(v0, v2));
-  const f2 sR = fma2(bc2(-2.f), v2, add2(v1, v3));
-  const f2 C1 = sub2(bc2(1.f), C0);
+  const f2 g = pk_sub(v2, v1);
+  const f2 sL = pk_fma(pk_bc(-2.f), v1, pk_add(v0, v2));
+  const f2 sR = pk_fma(pk_bc(-2.f), v2, pk_add(v1, v3));
+  const f2 C1 = pk_sub(pk_bc(1.f), C0);
   f2 a0, a1;
   if (BMODE == B0) {
     a0 = C0; a1 = C1;
   } else {
-    const f2 k2 = bc2(13.f / 12.f), e = bc2(eps);
-    const f2 eL = fma2(g, g, fma2(mul2(k2, sL), sL, e));
-    const f2 eR = fma2(g, g, fma2(mul2(k2, sR), sR, e));
+    const f2 k2 = pk_bc(13.f / 12.f), e = pk_bc(eps);
+    const f2 eL = pk_fma(g, g, pk_fma(pk_mul(k2, sL), sL, e));
+    const f2 eR = pk_fma(g, g, pk_fma(pk_mul(k2, sR), sR, e));
     if (BMODE == B2R) {
-      a0 = mul2(C0, mul2(eR, eR));
-      a1 = mul2(C1, mul2(eL, eL));
+      a0 = pk_mul(C0, pk_mul(eR, eR));
+      a1 = pk_mul(C1, pk_mul(eL, eL));
     } else {
-      const f2 inv = rcp2(make_float2(fmaxf(eL.x, eR.x), fmaxf(eL.y, eR.y)));
-      const f2 rL = mul2(eL, inv), rR = mul2(eR, inv);
+      const f2 inv = pk_rcp(make_float2(fmaxf(eL.x, eR.x), fmaxf(eL.y, eR.y)));
+      const f2 rL = pk_mul(eL, inv), rR = pk_mul(eR, inv);
       if (BMODE == B2) {
-        a0 = mul2(mul2(C0, rR), rR);
-        a1 = mul2(mul2(C1, rL), rL);
+        a0 = pk_mul(pk_mul(C0, rR), rR);
+        a1 = pk_mul(pk_mul(C1, rL), rL);
       } else {
-        const f2 b = bc2(beta);
-        const f2 lR = mul2(b, make_float2(lg2_approx(rR.x), lg2_approx(rR.y)));
-        const f2 lL = mul2(b, make_float2(lg2_approx(rL.x), lg2_approx(rL.y)));
-        a0 = mul2(C0, make_float2(ex2_approx(lR.x), ex2_approx(lR.y)));
-        a1 = mul2(C1, make_float2(ex2_approx(lL.x), ex2_approx(lL.y)));
+        const f2 b = pk_bc(beta);
+        const f2 lR = pk_mul(b, make_float2(lg2_approx(rR.x), lg2_approx(rR.y)));
+        const f2 lL = pk_mul(b, make_float2(lg2_approx(rL.x), lg2_approx(rL.y)));
+        a0 = pk_mul(C0, make_float2(ex2_approx(lR.x), ex2_approx(lR.y)));
+        a1 = pk_mul(C1, make_float2(ex2_approx(lL.x), ex2_approx(lL.y)));
       }
     }
   }
-  const f2 mix = mul2(fma2(a0, sL, mul2(a1, sR)), rcp2(add2(a0, a1)));
-  return fma2(h, mix, fma2(g, t, v1));
+  const f2 mix = pk_mul(pk_fma(a0, sL, pk_mul(a1, sR)), pk_rcp(pk_add(a0, a1)));
+  return pk_fma(h, mix, pk_fma(g, t, v1));
 }
 
 template <int BMODE>
@@ -330,7 +313,7 @@ __global__ void __launch_bounds__(RS_THREADS) resample_tiled_kernel(ResampleArgs
         const f2 zz = weno1d_at2<BMODE>(
             make_float2(w0[k], w0[kb]), make_float2(w0[k + RS_WC], w0[kb + RS_WC]),
             make_float2(w0[k + 2 * RS_WC], w0[kb + 2 * RS_WC]),
-            make_float2(w0[k + 3 * RS_WC], w0[kb + 3 * RS_WC]), bc2(ty), bc2(C0), bc2(h), eps,
+            make_float2(w0[k + 3 * RS_WC], w0[kb + 3 * RS_WC]), pk_bc(ty), pk_bc(C0), pk_bc(h), eps,
             beta);
         z[r][k] = zz.x;
         if (two) z[r][k + 32] = zz.y;
