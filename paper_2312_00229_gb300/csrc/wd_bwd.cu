@@ -39,6 +39,7 @@
 // values a step needs are loaded three (input rows: two or four) steps
 // before it.
 #include "wd_bwd.h"
+#include "wd_packed.cuh"
 
 namespace wdweno {
 
@@ -146,52 +147,76 @@ __device__ __forceinline__ Sten sten_s(const float* xr, float am1, float a0, flo
   return q;
 }
 
-__device__ __forceinline__ float4 indicators(const Sten& q, float kap, float eps) {
-  float si[4];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const float ks = kap * q.s[k];
-    si[k] = fmaf(q.g[k], q.g[k], fmaf(ks, ks, eps));
-  }
-  return make_float4(si[0], si[1], si[2], si[3]);
+// The helpers below work on the direction pairs (0, 1) and (2, 3) with the
+// packed two-lane FP32 instructions of wd_packed.cuh; every lane takes the
+// scalar expression's operations in the scalar order.
+__device__ __forceinline__ f2 lo2(const float4& v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ f2 hi2(const float4& v) { return make_float2(v.z, v.w); }
+__device__ __forceinline__ f2 pair(const float* v, int p) {
+  return make_float2(v[2 * p], v[2 * p + 1]);
 }
 
-__device__ __forceinline__ float comp(const float4& v, int d) {
-  return d == 0 ? v.x : (d == 1 ? v.y : (d == 2 ? v.z : v.w));
+// SI_k = g_k^2 + (kappa s_k)^2 + eps
+__device__ __forceinline__ float4 indicators(const Sten& q, float kap, float eps) {
+  f2 si[2];
+#pragma unroll
+  for (int p = 0; p < 2; ++p) {
+    const f2 g = pair(q.g, p);
+    const f2 ks = pk_mul(pk_bc(kap), pair(q.s, p));
+    si[p] = pk_fma(g, g, pk_fma(ks, ks, pk_bc(eps)));
+  }
+  return make_float4(si[0].x, si[0].y, si[1].x, si[1].y);
 }
 
 // D_k = own_k + w (n0 + n1 + n2 + n3)_k
 __device__ __forceinline__ void smooth(const float4& own, const float4& n0, const float4& n1,
                                        const float4& n2, const float4& n3, float w, float D[4]) {
-#pragma unroll
-  for (int d = 0; d < 4; ++d)
-    D[d] = fmaf(w, (comp(n0, d) + comp(n1, d)) + (comp(n2, d) + comp(n3, d)), comp(own, d));
+  const f2 W = pk_bc(w);
+  const f2 d01 =
+      pk_fma(W, pk_add(pk_add(lo2(n0), lo2(n1)), pk_add(lo2(n2), lo2(n3))), lo2(own));
+  const f2 d23 =
+      pk_fma(W, pk_add(pk_add(hi2(n0), hi2(n1)), pk_add(hi2(n2), hi2(n3))), hi2(own));
+  D[0] = d01.x; D[1] = d01.y; D[2] = d23.x; D[3] = d23.y;
 }
 
-// Normalised weights omega_k from D_k (Eqs. alpha, IzrazOmega2d).
+// Normalised weights omega_k from D_k (Eqs. alpha, IzrazOmega2d), and 1/D_k.
 template <int BMODE>
-__device__ __forceinline__ void weights(const float D[4], float beta, float om[4]) {
-  float al[4];
+__device__ __forceinline__ void weights(const float D[4], float beta, float om[4], float rD[4]) {
+  f2 al[2], rd[2];
+#pragma unroll
+  for (int p = 0; p < 2; ++p) rd[p] = pk_rcp(make_float2(D[2 * p], D[2 * p + 1]));
   if (BMODE == B0) {
-#pragma unroll
-    for (int k = 0; k < 4; ++k) al[k] = 1.f;
+    al[0] = al[1] = pk_bc(1.f);
   } else {
-    const float dmin = fminf(fminf(D[0], D[1]), fminf(D[2], D[3]));
+    const f2 dmin = pk_bc(fminf(fminf(D[0], D[1]), fminf(D[2], D[3])));
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const float r = dmin * rcp_approx(D[k]);
-      al[k] = BMODE == B2 ? r * r : ex2_approx(beta * lg2_approx(r));
+    for (int p = 0; p < 2; ++p) {
+      const f2 r = pk_mul(dmin, rd[p]);
+      if (BMODE == B2) {
+        al[p] = pk_mul(r, r);
+      } else {
+        const f2 l = pk_mul(pk_bc(beta), make_float2(lg2_approx(r.x), lg2_approx(r.y)));
+        al[p] = make_float2(ex2_approx(l.x), ex2_approx(l.y));
+      }
     }
   }
   // the largest alpha is 1, so the sum lies in [1, 4]
-  const float inv = rcp_approx((al[0] + al[1]) + (al[2] + al[3]));
+  const f2 inv = pk_bc(rcp_approx((al[0].x + al[0].y) + (al[1].x + al[1].y)));
 #pragma unroll
-  for (int k = 0; k < 4; ++k) om[k] = al[k] * inv;
+  for (int p = 0; p < 2; ++p) {
+    const f2 o = pk_mul(al[p], inv);
+    om[2 * p] = o.x; om[2 * p + 1] = o.y;
+    rD[2 * p] = rd[p].x; rD[2 * p + 1] = rd[p].y;
+  }
 }
 
 // p_k = (N0 + N1)/2 - s_k/8 (Eq. p)
-__device__ __forceinline__ float interp(const Sten& q, int k) {
-  return fmaf(-0.125f, q.s[k], 0.5f * q.M[k >> 1]);
+__device__ __forceinline__ void interp4(const Sten& q, float ip[4]) {
+#pragma unroll
+  for (int p = 0; p < 2; ++p) {
+    const f2 v = pk_fma(pk_bc(-0.125f), pair(q.s, p), pk_bc(0.5f * q.M[p]));
+    ip[2 * p] = v.x; ip[2 * p + 1] = v.y;
+  }
 }
 
 // p_bar and 2 D_bar of one blend point given its D and stencil data (D_bar
@@ -199,8 +224,8 @@ __device__ __forceinline__ float interp(const Sten& q, int k) {
 template <int BMODE>
 __device__ __forceinline__ void point_adjoint(const Sten& q, const float D[4], float beta,
                                               float ub, float4& pb4, float4& db4) {
-  float om[4], pb[4], db[4];
-  weights<BMODE>(D, beta, om);
+  float om[4], rD[4];
+  weights<BMODE>(D, beta, om, rD);
   // p_k - u from differences of the stencil data, so that no two O(1)
   // values cancel: d_k = p_k - p_0 = (M_k - M_0)/2 - (s_k - s_0)/8 and
   // u - p_0 = sum_l omega_l d_l, so p_k - u = d_k - sum_l omega_l d_l.
@@ -209,15 +234,18 @@ __device__ __forceinline__ void point_adjoint(const Sten& q, const float D[4], f
   const float d2 = fmaf(-0.125f, q.s[2] - q.s[0], hM);
   const float d3 = fmaf(-0.125f, q.s[3] - q.s[0], hM);
   const float v = fmaf(om[1], d1, fmaf(om[2], d2, om[3] * d3));
-  const float pu[4] = {-v, d1 - v, d2 - v, d3 - v};
+  const f2 pu[2] = {make_float2(-v, d1 - v), pk_sub(make_float2(d2, d3), pk_bc(v))};
   const float ubb = -ub * (2.f * beta);
+  f2 pb[2], db[2];
 #pragma unroll
-  for (int kk = 0; kk < 4; ++kk) {
-    pb[kk] = ub * om[kk];
-    db[kk] = BMODE == B0 ? 0.f : ubb * om[kk] * pu[kk] * rcp_approx(D[kk]);
+  for (int p = 0; p < 2; ++p) {
+    const f2 o = pair(om, p);
+    pb[p] = pk_mul(pk_bc(ub), o);
+    db[p] = BMODE == B0 ? pk_bc(0.f)
+                        : pk_mul(pk_mul(pk_mul(pk_bc(ubb), o), pu[p]), pair(rD, p));
   }
-  pb4 = make_float4(pb[0], pb[1], pb[2], pb[3]);
-  db4 = make_float4(db[0], db[1], db[2], db[3]);
+  pb4 = make_float4(pb[0].x, pb[0].y, pb[1].x, pb[1].y);
+  db4 = make_float4(db[0].x, db[0].y, db[1].x, db[1].y);
 }
 
 // Node coefficients (N0, N1, N2) of the four stencils of a point; sb2 holds
@@ -225,12 +253,17 @@ __device__ __forceinline__ void point_adjoint(const Sten& q, const float D[4], f
 __device__ __forceinline__ void node_coefs(const Sten& q, const float4& pb, const float sb2[4],
                                            float k2, float c[4][3]) {
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const float pbar = comp(pb, k), sbar2 = sb2[k];
-    const float g2 = q.g[k] * sbar2, s2 = k2 * q.s[k] * sbar2;
-    c[k][0] = fmaf(0.375f, pbar, s2 - g2);
-    c[k][1] = fmaf(0.75f, pbar, fmaf(-2.f, s2, g2));
-    c[k][2] = fmaf(-0.125f, pbar, s2);
+  for (int p = 0; p < 2; ++p) {
+    const f2 pbar = p ? hi2(pb) : lo2(pb);
+    const f2 sb = pair(sb2, p);
+    const f2 g2 = pk_mul(pair(q.g, p), sb);
+    const f2 s2 = pk_mul(pk_mul(pk_bc(k2), pair(q.s, p)), sb);
+    const f2 c0 = pk_fma(pk_bc(0.375f), pbar, pk_sub(s2, g2));
+    const f2 c1 = pk_fma(pk_bc(0.75f), pbar, pk_fma(pk_bc(-2.f), s2, g2));
+    const f2 c2 = pk_fma(pk_bc(-0.125f), pbar, s2);
+    c[2 * p][0] = c0.x; c[2 * p + 1][0] = c0.y;
+    c[2 * p][1] = c1.x; c[2 * p + 1][1] = c1.y;
+    c[2 * p][2] = c2.x; c[2 * p + 1][2] = c2.y;
   }
 }
 
@@ -447,12 +480,14 @@ struct PlusSweep {
       smooth(R.SIX[sl.template m4<5>()][u], R.SIX[sl.template m4<6>()][u],
              R.SIX[sl.template m4<4>()][u], R.SIX[sl.template m4<5>()][u - 1],
              R.SIX[sl.template m4<5>()][u + 1], w, D);
-      weights<BMODE>(D, k.beta, om);
+      float rD[4], ip[4];
+      weights<BMODE>(D, k.beta, om, rD);
       const Sten q = sten_x(sl.template a<6>(), sl.template a<5>(), sl.template a<4>(),
                             sl.template a<3>());
+      interp4(q, ip);
       float x = 0.f;
 #pragma unroll
-      for (int d = 0; d < 4; ++d) x = fmaf(om[d], interp(q, d), x);
+      for (int d = 0; d < 4; ++d) x = fmaf(om[d], ip[d], x);
       *sl.template x<5>() = x;
     }
     // ---- "+" indicators, row r = s-7 ----
