@@ -36,7 +36,7 @@
 // are published per row in shared memory and gathered one step later.
 // In the middle of a band the steps run in groups of four with every ring
 // slot a compile-time constant and no stage guards (sweep_band); the global
-// values a step needs are loaded three (input rows: two or four) steps
+// values a step needs are loaded three to five (input rows: two or four) steps
 // before it.
 #include "wd_bwd.h"
 #include "wd_packed.cuh"
@@ -419,9 +419,8 @@ struct PlusSweep {
   GCol godd, gevn;  // fine column 2c + 1 (E and x points) and 2c (S points, samples)
   // carried from step to step
   float pf, pf2;              // input rows s+1, s+2 of the column
-  float ue, us, gx, ga;       // output gradients of the next step's rows
-  float ue2, us2, gx2, ga2;   // and of the step after
-  float ue3, us3, gx3, ga3;   // and of the one after that
+  // output gradients of the rows the next 5 steps use: [0] the next step's
+  float ue[5], us[5], gx[5], ga[5];
   float4 pe1, pe2, ps1, ps2;  // p_bar of the "+" points of rows s-10 (1), s-11 (2)
   float xacc[4], aacc[4];     // own-column accumulators: X_bar rows r-2 .. r+1,
                               // A_bar rows r-1 .. r+2 (r = the coefficient row)
@@ -455,13 +454,15 @@ struct PlusSweep {
     const float cur = pf;
     pf = pf2;
     pf2 = __ldg(xin + (int64_t)clampi(s + 2, 0, n - 1) * x_sh);
-    const float ue_s = ue, us_s = us, gx_s = gx, ga_s = ga;
-    ue = ue2; us = us2; gx = gx2; ga = ga2;
-    ue2 = ue3; us2 = us3; gx2 = gx3; ga2 = ga3;
-    ue3 = godd.template at<FULL>(2 * (s - 6));
-    us3 = gevn.template at<FULL>(2 * (s - 6) + 1);
-    gx3 = godd.template at<FULL>(2 * (s - 10) + 1);
-    ga3 = gevn.template at<FULL>(2 * (s - 9));
+    const float ue_s = ue[0], us_s = us[0], gx_s = gx[0], ga_s = ga[0];
+#pragma unroll
+    for (int j = 0; j + 1 < 5; ++j) {
+      ue[j] = ue[j + 1]; us[j] = us[j + 1]; gx[j] = gx[j + 1]; ga[j] = ga[j + 1];
+    }
+    ue[5 - 1] = godd.template at<FULL>(2 * (s - 9 + 5));
+    us[5 - 1] = gevn.template at<FULL>(2 * (s - 9 + 5) + 1);
+    gx[5 - 1] = godd.template at<FULL>(2 * (s - 13 + 5) + 1);
+    ga[5 - 1] = gevn.template at<FULL>(2 * (s - 12 + 5));
     __syncthreads();
     *sl.template a<0>() = cur;
 
@@ -610,26 +611,21 @@ __global__ void __launch_bounds__(NT1, NT1 == NT_NARROW ? 3 : 2)
   const int n = sw.n;
   sw.pf = __ldg(sw.xin + (int64_t)clampi(s_begin, 0, n - 1) * sw.x_sh);
   sw.pf2 = __ldg(sw.xin + (int64_t)clampi(s_begin + 1, 0, n - 1) * sw.x_sh);
-  sw.ue = sw.godd.template at<false>(2 * (s_begin - 9));
-  sw.us = sw.gevn.template at<false>(2 * (s_begin - 9) + 1);
-  sw.gx = sw.godd.template at<false>(2 * (s_begin - 13) + 1);
-  sw.ga = sw.gevn.template at<false>(2 * (s_begin - 12));
-  sw.ue2 = sw.godd.template at<false>(2 * (s_begin - 8));
-  sw.us2 = sw.gevn.template at<false>(2 * (s_begin - 8) + 1);
-  sw.gx2 = sw.godd.template at<false>(2 * (s_begin - 12) + 1);
-  sw.ga2 = sw.gevn.template at<false>(2 * (s_begin - 11));
-  sw.ue3 = sw.godd.template at<false>(2 * (s_begin - 7));
-  sw.us3 = sw.gevn.template at<false>(2 * (s_begin - 7) + 1);
-  sw.gx3 = sw.godd.template at<false>(2 * (s_begin - 11) + 1);
-  sw.ga3 = sw.gevn.template at<false>(2 * (s_begin - 10));
+#pragma unroll
+  for (int j = 0; j < 5; ++j) {
+    sw.ue[j] = sw.godd.template at<false>(2 * (s_begin - 9 + j));
+    sw.us[j] = sw.gevn.template at<false>(2 * (s_begin - 9 + j) + 1);
+    sw.gx[j] = sw.godd.template at<false>(2 * (s_begin - 13 + j) + 1);
+    sw.ga[j] = sw.gevn.template at<false>(2 * (s_begin - 12 + j));
+  }
   sw.pe1 = sw.pe2 = sw.ps1 = sw.ps2 = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
   for (int j = 0; j < 4; ++j) sw.xacc[j] = sw.aacc[j] = 0.f;
   // FULL steps: every stage live and every output row written (s in
   // [a0 + 13, a1 + 7]), and the output-gradient rows a step loads inside
-  // the output (2 (s - 10) + 1 >= 0, 2 (s - 6) + 1 < orows)
-  const int s_lo = max(sw.a0 + 13, 10);
-  const int s_hi = min(sw.a1 + 7, sw.gevn.orows >= 2 ? (sw.gevn.orows - 2) / 2 + 6 : 5);
+  // the output (2 (s - 13 + 5) + 1 >= 0, 2 (s - 9 + 5) + 1 < orows)
+  const int s_lo = max(sw.a0 + 13, 8);
+  const int s_hi = min(sw.a1 + 7, sw.gevn.orows >= 2 ? (sw.gevn.orows - 2) / 2 + 4 : 3);
   sweep_band(sw, &R.A[0][sw.u], &R.X[0][sw.u], s_begin, s_end, s_lo, s_hi);
 }
 
