@@ -16,6 +16,7 @@
 #pragma once
 
 #include "wd_fwd_tile.cuh"
+#include "wd_packed.cuh"
 
 namespace wdweno {
 namespace fwd_tile {
@@ -157,10 +158,12 @@ struct FwdTile2 {
     // ---- stage 5: E(s-6, c0..c1) and S(s-7, c0..c1) ------------------------
     if (FULL || (rs >= 6 && rs <= H + 5)) {
       const float4 v = ex.VS[PH ^ 1][t + 2];  // VS of column c0 + 2 (slot of step s-1)
-      const float vs[4] = {v.x, v.y, v.z, v.w};
       float D1[4];
-#pragma unroll
-      for (int d = 0; d < 4; ++d) D1[d] = fmaf(w, vs[d], C.DEp1[d]);
+      {
+        const f2 a = pk_fma(pk_bc(w), make_float2(v.x, v.y), make_float2(C.DEp1[0], C.DEp1[1]));
+        const f2 b = pk_fma(pk_bc(w), make_float2(v.z, v.w), make_float2(C.DEp1[2], C.DEp1[3]));
+        D1[0] = a.x; D1[1] = a.y; D1[2] = b.x; D1[3] = b.y;
+      }
       const float e0 = blend4<BMODE>(C.DE0[0], C.DE0[1], C.DE0[2], C.DE0[3], C.pE[0][0],
                                      C.pE[0][1], C.pE[0][2], C.pE[0][3], C.pE[0][4],
                                      C.pE[0][5], k.beta);
@@ -171,10 +174,12 @@ struct FwdTile2 {
     }
     if (FULL || rs >= 7) {
       const float4 v = ex.VE[PH ^ 1][t];  // VE of column c0 - 1
-      const float ve[4] = {v.x, v.y, v.z, v.w};
       float D0[4];
-#pragma unroll
-      for (int d = 0; d < 4; ++d) D0[d] = fmaf(w, ve[d], C.DSp0[d]);
+      {
+        const f2 a = pk_fma(pk_bc(w), make_float2(v.x, v.y), make_float2(C.DSp0[0], C.DSp0[1]));
+        const f2 b = pk_fma(pk_bc(w), make_float2(v.z, v.w), make_float2(C.DSp0[2], C.DSp0[3]));
+        D0[0] = a.x; D0[1] = a.y; D0[2] = b.x; D0[3] = b.y;
+      }
       const float4 ps0 = ex.PS[PH][0][t], ps1 = ex.PS[PH][1][t], ps2 = ex.PS[PH][2][t];
       const float p0[6] = {ps0.x, ps0.y, ps0.z, ps0.w, ps1.x, ps1.y};
       const float p1[6] = {ps1.z, ps1.w, ps2.x, ps2.y, ps2.z, ps2.w};
@@ -237,10 +242,19 @@ struct FwdTile2 {
       for (int u = 0; u < 2; ++u) {
         float D[4];
 #pragma unroll
-        for (int d = 0; d < 4; ++d) {
-          const float hl = u == 0 ? hl0[d] : C.SI[Q][0][d];  // row s-4 at column c - 1
-          const float hr = u == 0 ? C.SI[Q][1][d] : hr1[d];  // row s-4 at column c + 1
-          D[d] = fmaf(w, C.SI[PH][u][d] + (hl + hr), C.P[u][d]);
+        for (int p = 0; p < 2; ++p) {
+          const int d = 2 * p;
+          // row s-4 at columns c - 1 and c + 1
+          const f2 hl = u == 0 ? make_float2(hl0[d], hl0[d + 1])
+                               : make_float2(C.SI[Q][0][d], C.SI[Q][0][d + 1]);
+          const f2 hr = u == 0 ? make_float2(C.SI[Q][1][d], C.SI[Q][1][d + 1])
+                               : make_float2(hr1[d], hr1[d + 1]);
+          const f2 v = pk_fma(pk_bc(w),
+                              pk_add(make_float2(C.SI[PH][u][d], C.SI[PH][u][d + 1]),
+                                     pk_add(hl, hr)),
+                              make_float2(C.P[u][d], C.P[u][d + 1]));
+          D[d] = v.x;
+          D[d + 1] = v.y;
         }
         const float* px = C.px[u];
         x4[u] = blend4<BMODE>(D[0], D[1], D[2], D[3], px[0], px[1], px[2], px[3], px[4], px[5],
@@ -255,7 +269,13 @@ struct FwdTile2 {
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
 #pragma unroll
-        for (int d = 0; d < 4; ++d) C.P[u][d] = fmaf(w, C.SI[Q][u][d], C.SI[PH][u][d]);
+        for (int p = 0; p < 2; ++p) {
+          const int d = 2 * p;
+          const f2 v = pk_fma(pk_bc(w), make_float2(C.SI[Q][u][d], C.SI[Q][u][d + 1]),
+                              make_float2(C.SI[PH][u][d], C.SI[PH][u][d + 1]));
+          C.P[u][d] = v.x;
+          C.P[u][d + 1] = v.y;
+        }
         C.px[u][0] = a3[u + 2] + a2[u + 3];  // N0 + N1 of the (1,1) diagonal pair
         C.px[u][1] = a3[u + 3] + a2[u + 2];  // N0 + N1 of the (1,-1) pair
         C.px[u][2] = C.S1[PH][u + 1];
@@ -344,9 +364,14 @@ struct FwdTile2 {
         C.a5c[u] = a5[u + 2];
         C.x6[u] = x6;
 #pragma unroll
-        for (int d = 0; d < 4; ++d) {
-          VSo[u][d] = C.SIS[Q][u][d] + SIS[d];
-          VEo[u][d] = C.SIE[Q][u][d] + SIE[d];
+        for (int p = 0; p < 2; ++p) {
+          const int d = 2 * p;
+          const f2 vs = pk_add(make_float2(C.SIS[Q][u][d], C.SIS[Q][u][d + 1]),
+                               make_float2(SIS[d], SIS[d + 1]));
+          const f2 ve = pk_add(make_float2(C.SIE[Q][u][d], C.SIE[Q][u][d + 1]),
+                               make_float2(SIE[d], SIE[d + 1]));
+          VSo[u][d] = vs.x; VSo[u][d + 1] = vs.y;
+          VEo[u][d] = ve.x; VEo[u][d + 1] = ve.y;
         }
       }
       // Row-pair sums for Eq. (tezine): S rows r-1, r feed E(r); E rows
@@ -354,13 +379,23 @@ struct FwdTile2 {
       ex.VS[PH][t + 1] = make_float4(VSo[0][0], VSo[0][1], VSo[0][2], VSo[0][3]);
       ex.VE[PH][t + 1] = make_float4(VEo[1][0], VEo[1][1], VEo[1][2], VEo[1][3]);
 #pragma unroll
-      for (int d = 0; d < 4; ++d) {
-        const float dep0 = fmaf(w, VSo[0][d], C.SIE[PH][0][d]);
-        C.DE0[d] = fmaf(w, VSo[1][d], dep0);  // E(c0) reads VS of c0 and c1
-        C.DEp1[d] = fmaf(w, VSo[1][d], C.SIE[PH][1][d]);
-        C.DSp0[d] = fmaf(w, VEo[0][d], C.SIS[Q][0][d]);
-        const float dsp1 = fmaf(w, VEo[1][d], C.SIS[Q][1][d]);
-        C.DS1[d] = fmaf(w, VEo[0][d], dsp1);  // S(c1) reads VE of c1 and c0
+      for (int p = 0; p < 2; ++p) {
+        const int d = 2 * p;
+        const f2 W = pk_bc(w);
+        const f2 vs0 = make_float2(VSo[0][d], VSo[0][d + 1]);
+        const f2 vs1 = make_float2(VSo[1][d], VSo[1][d + 1]);
+        const f2 ve0 = make_float2(VEo[0][d], VEo[0][d + 1]);
+        const f2 ve1 = make_float2(VEo[1][d], VEo[1][d + 1]);
+        const f2 dep0 = pk_fma(W, vs0, make_float2(C.SIE[PH][0][d], C.SIE[PH][0][d + 1]));
+        const f2 de0 = pk_fma(W, vs1, dep0);  // E(c0) reads VS of c0 and c1
+        const f2 dep1 = pk_fma(W, vs1, make_float2(C.SIE[PH][1][d], C.SIE[PH][1][d + 1]));
+        const f2 dsp0 = pk_fma(W, ve0, make_float2(C.SIS[Q][0][d], C.SIS[Q][0][d + 1]));
+        const f2 dsp1 = pk_fma(W, ve1, make_float2(C.SIS[Q][1][d], C.SIS[Q][1][d + 1]));
+        const f2 ds1 = pk_fma(W, ve0, dsp1);  // S(c1) reads VE of c1 and c0
+        C.DE0[d] = de0.x; C.DE0[d + 1] = de0.y;
+        C.DEp1[d] = dep1.x; C.DEp1[d + 1] = dep1.y;
+        C.DSp0[d] = dsp0.x; C.DSp0[d + 1] = dsp0.y;
+        C.DS1[d] = ds1.x; C.DS1[d + 1] = ds1.y;
       }
     }
   }
