@@ -66,6 +66,7 @@ PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "zoom2x_fwd_4k_u8.md")
 KERNEL_SOURCES = ["paper_2312_00229_gb300/csrc/wd_fwd_tile.cuh",
                   "paper_2312_00229_gb300/csrc/wd_fwd_tile2.cuh",
                   "paper_2312_00229_gb300/csrc/wd_common.cuh",
+                  "paper_2312_00229_gb300/csrc/wd_packed.cuh",
                   "paper_2312_00229_gb300/csrc/wd_fwd_kernels.cuh"]
 
 
