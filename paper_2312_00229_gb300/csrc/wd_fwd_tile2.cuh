@@ -164,10 +164,10 @@ struct FwdTile2 {
         const f2 b = pk_fma(pk_bc(w), make_float2(v.z, v.w), make_float2(C.DEp1[2], C.DEp1[3]));
         D1[0] = a.x; D1[1] = a.y; D1[2] = b.x; D1[3] = b.y;
       }
-      const float e0 = blend4<BMODE>(C.DE0[0], C.DE0[1], C.DE0[2], C.DE0[3], C.pE[0][0],
+      const float e0 = blend4_pk<BMODE>(C.DE0[0], C.DE0[1], C.DE0[2], C.DE0[3], C.pE[0][0],
                                      C.pE[0][1], C.pE[0][2], C.pE[0][3], C.pE[0][4],
                                      C.pE[0][5], k.beta);
-      const float e1 = blend4<BMODE>(D1[0], D1[1], D1[2], D1[3], C.pE[1][0], C.pE[1][1],
+      const float e1 = blend4_pk<BMODE>(D1[0], D1[1], D1[2], D1[3], C.pE[1][0], C.pE[1][1],
                                      C.pE[1][2], C.pE[1][3], C.pE[1][4], C.pE[1][5], k.beta);
       const int rE = s - 6;  // fine row 2 rE: [A, E] of both columns
       if (FULL || (rE < n && 2 * rE < orows)) store_quad_row(oE, C.a5c[0], e0, C.a5c[1], e1);
@@ -183,9 +183,9 @@ struct FwdTile2 {
       const float4 ps0 = ex.PS[PH][0][t], ps1 = ex.PS[PH][1][t], ps2 = ex.PS[PH][2][t];
       const float p0[6] = {ps0.x, ps0.y, ps0.z, ps0.w, ps1.x, ps1.y};
       const float p1[6] = {ps1.z, ps1.w, ps2.x, ps2.y, ps2.z, ps2.w};
-      const float s0 = blend4<BMODE>(D0[0], D0[1], D0[2], D0[3], p0[0], p0[1], p0[2], p0[3],
+      const float s0 = blend4_pk<BMODE>(D0[0], D0[1], D0[2], D0[3], p0[0], p0[1], p0[2], p0[3],
                                      p0[4], p0[5], k.beta);
-      const float s1 = blend4<BMODE>(C.DS1[0], C.DS1[1], C.DS1[2], C.DS1[3], p1[0], p1[1],
+      const float s1 = blend4_pk<BMODE>(C.DS1[0], C.DS1[1], C.DS1[2], C.DS1[3], p1[0], p1[1],
                                      p1[2], p1[3], p1[4], p1[5], k.beta);
       const int rS = s - 7;  // fine row 2 rS + 1: [S, X] of both columns
       if (FULL || (rS < n && 2 * rS + 1 < orows))
@@ -257,7 +257,7 @@ struct FwdTile2 {
           D[d + 1] = v.y;
         }
         const float* px = C.px[u];
-        x4[u] = blend4<BMODE>(D[0], D[1], D[2], D[3], px[0], px[1], px[2], px[3], px[4], px[5],
+        x4[u] = blend4_pk<BMODE>(D[0], D[1], D[2], D[3], px[0], px[1], px[2], px[3], px[4], px[5],
                               k.beta);
       }
       const int xs = (s - 4) & 3;
