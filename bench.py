@@ -89,8 +89,9 @@ def parse_args():
                          "512x512x3 uint8 pixel art zoomed 8x by three 2x levels")
     ap.add_argument("--fused", action="store_true",
                     help="--case cascade8x: all levels in one persistent launch")
-    ap.add_argument("--tile-width", type=int, default=0, choices=[0, 119, 247],
-                    help="--case batched: output columns per CTA (0 = the library default)")
+    ap.add_argument("--tile-width", type=int, default=0, choices=[0, 119, 247, 118, 246],
+                    help="--case batched: output columns per CTA (0 = the library default; "
+                         "118 / 246: two coarse columns per thread)")
     ap.add_argument("--batch", type=int, default=None,
                     help="images per step of --case fwdbwd (default 32, the workload) or "
                          "--case batched (default 256, the workload)")
