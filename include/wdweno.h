@@ -277,12 +277,12 @@ int weno_zoom2x_batched_noalloc(int count, const weno_image* d_in, weno_dtype in
  * writes one float per thread to `out` (device buffer of >= blocks x 256
  * floats, caller-owned).  Timing the launch on `stream` gives the measured
  * FP32 operation rate beside the nominal one (SMs x 128 lanes x clock).
- * Returns WENO_OK, WENO_EINVAL (blocks or iters < 1, null out) or
- * WENO_ECUDA. */
+ * Returns WENO_OK, WENO_EINVAL (blocks or iters outside 1 .. 2^23, null
+ * out) or WENO_ECUDA. */
 int weno_fp32_probe(int blocks, int iters, float* out, void* stream);
 
 /* FP32 operations (one per fused multiply-add) one weno_fp32_probe launch
- * performs. */
+ * performs; -1 for arguments weno_fp32_probe rejects. */
 long long weno_fp32_probe_ops(int blocks, int iters);
 
 #ifdef __cplusplus

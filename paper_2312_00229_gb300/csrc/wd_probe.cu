@@ -33,13 +33,18 @@ __global__ void __launch_bounds__(256) k_fp32_probe(int iters, float a, float b,
 }  // namespace
 }  // namespace wdweno
 
+// Largest accepted blocks and iters (the operation count stays below 2^63).
+constexpr int kProbeMax = 1 << 23;
+
 extern "C" int weno_fp32_probe(int blocks, int iters, float* out, void* stream) {
-  if (blocks < 1 || iters < 1 || !out) return WENO_EINVAL;
+  if (blocks < 1 || iters < 1 || blocks > kProbeMax || iters > kProbeMax || !out)
+    return WENO_EINVAL;
   wdweno::k_fp32_probe<<<blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(
       iters, 0.999999f, 1e-6f, out);
   return cudaGetLastError() == cudaSuccess ? WENO_OK : WENO_ECUDA;
 }
 
 extern "C" long long weno_fp32_probe_ops(int blocks, int iters) {
+  if (blocks < 1 || iters < 1 || blocks > kProbeMax || iters > kProbeMax) return -1;
   return (long long)blocks * 256 * iters * 8 * wdweno::CHAINS;
 }

@@ -208,3 +208,5 @@ def test_fp32_probe_rejects_bad_arguments_and_counts_ops():
     assert B.weno_fp32_probe(1, 1, None, None) == B.WENO_EINVAL
     # 256 threads x 8 rounds x 16 chains per iteration
     assert B.weno_fp32_probe_ops(3, 5) == 3 * 256 * 5 * 8 * 16
+    assert B.weno_fp32_probe(1 << 25, 1, 0x100, None) == B.WENO_EINVAL
+    assert B.weno_fp32_probe_ops(1, 1 << 25) == -1 and B.weno_fp32_probe_ops(0, 1) == -1
