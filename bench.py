@@ -78,6 +78,8 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--skip-extras", action="store_true",
                     help="headline only (no fwd+bwd / batched / sweep / cascade)")
+    ap.add_argument("--log", default=None,
+                    help="also append the JSON line to this JSON-lines results file")
     ap.add_argument("--case", choices=["headline", "fwd4k", "resample3x", "fwdbwd", "batched",
                                        "cascade8x"],
                     default="headline",
@@ -356,6 +358,21 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # GPU timing helpers
 # ---------------------------------------------------------------------------
+class nvtx_range:
+    """An NVTX range around a phase of the run, visible on a profiler's
+    timeline (nothing when no profiler listens)."""
+
+    def __init__(self, torch, name):
+        self.torch, self.name = torch, name
+
+    def __enter__(self):
+        self.torch.cuda.nvtx.range_push(self.name)
+
+    def __exit__(self, *exc):
+        self.torch.cuda.nvtx.range_pop()
+        return False
+
+
 def time_graph(torch, fn_list, reps, warm=3):
     """Captures fn_list (callables enqueuing work) into one graph, replays it
     `reps` times, returns seconds per replay (CUDA events)."""
@@ -449,11 +466,12 @@ def run_ours(args):
     barrier(world)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(steps):
-        graph.replay()
-    e1.record()
-    torch.cuda.synchronize()
+    with nvtx_range(torch, "headline timed region"):
+        e0.record()
+        for _ in range(steps):
+            graph.replay()
+        e1.record()
+        torch.cuda.synchronize()
     barrier(world)
     clocks = sampler.stop()
     t_local = e0.elapsed_time(e1) / 1e3
@@ -525,11 +543,12 @@ def run_ours(args):
     pipe.flush()
     k_e2e = 1  # steps of FRAMES_PER_STEP frames each
     barrier(world)
-    t0 = time.perf_counter()
-    for j in range(k_e2e * FRAMES_PER_STEP):
-        pipe.submit(x_pin, o_pins[j % depth])
-    pipe.flush()
-    t_e2e = max_over_ranks(world, time.perf_counter() - t0, dev)
+    with nvtx_range(torch, "end-to-end pipeline"):
+        t0 = time.perf_counter()
+        for j in range(k_e2e * FRAMES_PER_STEP):
+            pipe.submit(x_pin, o_pins[j % depth])
+        pipe.flush()
+        t_e2e = max_over_ranks(world, time.perf_counter() - t0, dev)
     line["e2e"] = {"value": round(world * k_e2e * FRAMES_PER_STEP * OUT_PX / t_e2e / 1e9, 4),
                    "unit": "Gpix/s",
                    "h2d_bytes_per_step": int(x_host.numel()) * FRAMES_PER_STEP,
@@ -554,12 +573,20 @@ def run_ours(args):
     torch.cuda.empty_cache()
 
     if not args.skip_extras:
-        line.update(extras(torch, np, api, scenes, dev, world, hbm_peak))
+        with nvtx_range(torch, "extras"):
+            line.update(extras(torch, np, api, scenes, dev, world, hbm_peak))
 
     if rank == 0:
         A01 = scenes.planar(img).astype(np.float64) / 255.0
         line["cpu_baseline"] = cpu_baseline(A01)
+        props = torch.cuda.get_device_properties(dev)
+        line["system"] = {"gpu": props.name, "sms": props.multi_processor_count,
+                          "host_cores": os.cpu_count(), "seed": scenes.seed_for(4),
+                          "torch": torch.__version__, "cuda": torch.version.cuda}
         print(json.dumps(line), flush=True)
+        if args.log:
+            with open(args.log, "a") as fh:
+                fh.write(json.dumps(line) + "\n")
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
