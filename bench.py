@@ -80,19 +80,20 @@ def parse_args():
                     help="headline only (no fwd+bwd / batched / sweep / cascade)")
     ap.add_argument("--log", default=None,
                     help="also append the JSON line to this JSON-lines results file")
-    ap.add_argument("--case", choices=["headline", "fwd4k", "resample3x", "fwdbwd", "batched",
-                                       "cascade8x"],
+    ap.add_argument("--case", choices=["headline", "fwd4k", "fwd1080", "resample3x", "fwdbwd",
+                                       "batched", "cascade8x"],
                     default="headline",
                     help="run one workload alone (for profiling) instead of the headline "
                          "line: fwd4k = the headline forward launch, eager, over the rotating "
-                         "buffer sets; resample3x = 1920x1080x3 uint8 -> 5760x3240 tensor "
+                         "buffer sets; fwd1080 = 1920x1080x3 uint8 -> 3840x2160 over 16 "
+                         "rotating sets (--tile-width picks the tile); resample3x = 1920x1080x3 uint8 -> 5760x3240 tensor "
                          "WENO; fwdbwd = one autograd step on Bx3x512x512 FP32; batched = "
                          "one persistent launch over B uneven FP16 RGB images; cascade8x = "
                          "512x512x3 uint8 pixel art zoomed 8x by three 2x levels")
     ap.add_argument("--fused", action="store_true",
                     help="--case cascade8x: all levels in one persistent launch")
     ap.add_argument("--tile-width", type=int, default=0, choices=[0, 119, 247, 118, 246],
-                    help="--case batched: output columns per CTA (0 = the library default; "
+                    help="--case batched / fwd1080: output columns per CTA (0 = the library default; "
                          "118 / 246: two coarse columns per thread)")
     ap.add_argument("--batch", type=int, default=None,
                     help="images per step of --case fwdbwd (default 32, the workload) or "
@@ -804,6 +805,19 @@ def run_case(args):
             api.zoom2x_fwd(xs[i], out=outs[i], rows_per_tile=shape[0], tile_width=shape[1])
         work = (f"{W}x{H}x{C} uint8 -> {2 * W}x{2 * H}, {ROTATING_SETS} rotating buffer sets, "
                 f"tile shape {shape[0] or 'default'} rows x {shape[1] or 'default'} columns")
+    elif args.case == "fwd1080":
+        hd = torch.from_numpy(scenes.planar(scenes.piecewise_smooth(1080, 1920,
+                                                                    seed=scenes.seed_for(2))))
+        xs = [hd.to(dev) for _ in range(16)]
+        outs = [torch.empty(3, 2160, 3840, dtype=torch.uint8, device=dev) for _ in range(16)]
+        it = [0]
+
+        def step():
+            i = it[0] % 16
+            it[0] += 1
+            api.zoom2x_fwd(xs[i], out=outs[i], rows_per_tile=0, tile_width=args.tile_width)
+        work = (f"1920x1080x3 uint8 -> 3840x2160, 16 rotating buffer sets, tile width "
+                f"{args.tile_width or 'default'}")
     elif args.case == "resample3x":
         hd = torch.from_numpy(scenes.planar(scenes.piecewise_smooth(
             1080, 1920, seed=scenes.seed_for(2)))).to(dev)
